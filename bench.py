@@ -1,0 +1,406 @@
+#!/usr/bin/env python
+"""Throughput of the micromagnetic hot path on one GB300 (or N independent replicas).
+
+Workload (default): the 512 x 512 x 16 permalloy film with 2 nm cells
+(padded FFT grid 1024 x 1024 x 32), Ms = 8e5 A/m, A = 1.3e-11 J/m,
+alpha = 0.5, a seeded vortex with 5 % noise, relaxed with adaptive RKF45
+(tol 1e-5) through the library's relax() entry point.  One step = one
+accepted RKF45 step of relax(): six stages, each a full demag + exchange
+field evaluation fused with the LLG right-hand side, the device-side step
+controller, and relax()'s torque check every ten trials.
+
+Reported: field evals/s (one demag + exchange evaluation of the whole mesh)
+as ``value``, LLG Mcell-steps/s, the roofline of the dominant kernel (its
+launches timed with CUDA events on the library's stream inside the timed
+region), clocks sampled during the timed region, an end-to-end number
+through the public API with host buffers, and the CPU oracle timed on a
+bounded sample.  ``--impl reference`` times the oracle instead.
+
+Multi-GPU (torchrun): the method runs on one GPU; N ranks run N independent
+replicas (one per GPU, no data exchange) and ``value`` sums their work over
+the slowest rank's time.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as wl  # noqa: E402
+
+METRIC = "demag+exch field evals/s & LLG Mcell-steps/s, % HBM roofline, vs FP64 oracle"
+UNIT = "field evals/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--workload", choices=["film512"], default="film512")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=150.0, help="seconds of oracle work for the reference arm")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- helpers
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2606_01114_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, precision):
+    """DRAM bytes per launch of ``kernel`` from the committed ncu summary, or
+    None when the kernel sources changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except Exception:
+        return None
+    e = t.get(f"{kernel}/{precision}")
+    if not e or e.get("source_sha") != source_hash():
+        return None
+    return float(e["bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(kind, n, s, Ms_cell=False):
+    """Bytes one launch of kernel class ``kind`` must move (s = element size).
+
+    Demag passes (Hx = nx+1 kept x frequencies, Py = 2 ny, Pz = 2 nz):
+      xfwd  reads M (3 N s), writes 3 nz ny Hx complex
+      yfwd  reads 3 nz ny Hx, writes 3 nz Py Hx complex
+      zconv reads and writes 3 nz Py Hx complex, reads the kernel octant
+            6 (Pz/2+1)(Py/2+1) Hx reals
+      yinv  mirror of yfwd;  xinv mirror of xfwd
+    RKF45 stage (average of its six launches): 42 vector fields of 3 N s
+    in total per step (m_in, H_d, m0, the stage slopes the tableau needs,
+    k_s and the next trial state)."""
+    nx, ny, nz = n
+    N = nx * ny * nz
+    Hx = nx + 1 if nx > 1 else 1
+    Py = 2 * ny if ny > 1 else 1
+    Pz = 2 * nz if nz > 1 else 1
+    c = 2 * s
+    small = 3 * nz * ny * Hx * c
+    big = 3 * nz * Py * Hx * c
+    vec = 3 * N * s
+    ms = N * s if Ms_cell else 0
+    return {
+        "xfwd": vec + ms + small,
+        "yfwd": small + big,
+        "zconv": 2 * big + 6 * (Pz // 2 + 1) * (Py // 2 + 1) * Hx * s,
+        "yinv": small + big,
+        "xinv": small + vec,
+        "stage": 42 * vec / 6.0,
+    }.get(kind)
+
+
+# ------------------------------------------------------------ CPU oracle
+def oracle_setup(w):
+    from oracle import micromag
+    t0 = time.perf_counter()
+    p = micromag.Problem(w["n"], w["d"], Ms=w["Ms"], A=w["A"], alpha=w["alpha"])
+    nh = p.kernel_hat()
+    p.kernel_hat = lambda: nh          # keep the transformed kernel (setup, not timed)
+    return p, time.perf_counter() - t0
+
+
+def oracle_field_eval(p, m):
+    return p.demag_fft(m) + p.exchange(m)
+
+
+def cpu_baseline(w, m):
+    p, setup_s = oracle_setup(w)
+    t0 = time.perf_counter()
+    oracle_field_eval(p, m)
+    dt = time.perf_counter() - t0
+    n = w["n"]
+    return {"value": 1.0 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"one demag + exchange field evaluation of the {n[0]}x{n[1]}x{n[2]} film, float64 numpy "
+                       f"(numpy FFT, one thread), {dt:.1f} s; Newell kernel setup ({setup_s:.0f} s) excluded"),
+            "llg_mcell_steps_per_s": (1.0 / dt) / 6.0 * (n[0] * n[1] * n[2]) / 1e6}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = wl.WORKLOADS[args.workload]
+    n = w["n"]
+    m = wl.vortex(n, w["d"], noise=0.05, seed=1)
+    p, setup_s = oracle_setup(w)
+    t0 = time.perf_counter()
+    oracle_field_eval(p, m)                     # warm-up (one evaluation at most)
+    t_eval = time.perf_counter() - t0
+    steps = max(1, min(args.steps, int(args.cpu_budget // max(t_eval, 1e-3))))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle_field_eval(p, m)
+    el = time.perf_counter() - t0
+    value = steps / el
+    sample = (f"{steps} demag + exchange field evaluations of the {n[0]}x{n[1]}x{n[2]} film (of {args.steps} "
+              f"requested, capped to ~{args.cpu_budget:.0f} s of oracle work), float64 numpy, one thread; "
+              f"one warm-up evaluation; Newell kernel setup ({setup_s:.0f} s) excluded")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": steps, "warmup": 1, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "film512: 512x512x16 cells of 2 nm, permalloy, alpha 0.5, seeded vortex + 5% noise",
+                   "what": "CPU oracle field evaluation"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import torch
+    import paper_2606_01114_gb300 as mm
+    from paper_2606_01114_gb300 import build as _build
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    else:
+        dist = None
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (no CPU fallback)")
+    torch.cuda.set_device(local)
+    _build.build()
+    w = wl.WORKLOADS[args.workload]
+    n, d = w["n"], w["d"]
+    N = n[0] * n[1] * n[2]
+    prec = mm.MM_F64 if args.precision == "f64" else mm.MM_F32
+    tdtype = torch.float64 if prec == mm.MM_F64 else torch.float32
+    s = 8 if prec == mm.MM_F64 else 4
+    stream = torch.cuda.current_stream()
+    ctx = mm.mm_init_mesh(*n, *d, precision=prec, stream=stream)
+    mm.mm_set_material(ctx, w["Ms"], w["A"], w["alpha"], w["Ku"])
+    m_host = wl.vortex(n, d, noise=0.05, seed=1)
+    m = torch.tensor(m_host, dtype=tdtype, device="cuda")
+
+    def relax(steps):
+        try:
+            mm.mm_relax(ctx, m, t_max=5e-9, torque_tol=0.0, max_steps=steps)
+        except mm.MMError as e:          # stopping on the step cap is the expected outcome here
+            if e.code != mm.MM_ERR_NOT_CONVERGED:
+                raise
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # warm-up
+    relax(args.warmup)
+    torch.cuda.synchronize()
+    # timed region: device-resident input, kernel timing on the library's stream
+    mm.mm_enable_kernel_timing(ctx, True)
+    launches0 = mm.mm_kernel_launches(ctx)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    relax(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    launches = mm.mm_kernel_launches(ctx) - launches0
+    accepted, rejected, t_sim, dt_last = mm.mm_step_stats(ctx)
+    ktimes = {name: mm.mm_kernel_time(ctx, k) for k, name in enumerate(mm.KERNEL_NAMES)}
+    mm.mm_enable_kernel_timing(ctx, False)
+    evals = ktimes["zconv"][1]           # one z-pass launch per demag evaluation
+    tot = torch.tensor([ms, float(evals), float(accepted)], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        mx = tot.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm_ = tot.clone()
+        dist.all_reduce(sm_, op=dist.ReduceOp.SUM)
+        ms_max, evals_all, acc_all = float(mx[0]), float(sm_[1]), float(sm_[2])
+    else:
+        ms_max, evals_all, acc_all = ms, float(evals), float(accepted)
+    value = evals_all / (ms_max / 1e3)
+    mcell = acc_all * N / (ms_max / 1e3) / 1e6
+
+    # roofline of the dominant kernel (largest share of device time)
+    peak, peak_src = load_peaks()
+    dom = max(("xfwd", "yfwd", "zconv", "yinv", "xinv", "stage"), key=lambda k: ktimes[k][0])
+    tot_ms, nl = ktimes[dom]
+    avg_s = tot_ms / 1e3 / max(nl, 1)
+    algo = algorithmic_bytes(dom, n, s)
+    achieved = algo / avg_s / 1e9
+    traffic = ncu_traffic(dom, args.precision)
+    kernel_share = {k: round(v[0] / max(sum(x[0] for x in ktimes.values()), 1e-9), 4) for k, v in ktimes.items()}
+    per_kernel = {}
+    for k in ("xfwd", "yfwd", "zconv", "yinv", "xinv", "stage"):
+        t_ms, cnt = ktimes[k]
+        if cnt:
+            b = algorithmic_bytes(k, n, s)
+            per_kernel[k] = {"launches": cnt, "avg_us": round(1e3 * t_ms / cnt, 2),
+                             "algo_MB": round(b / 1e6, 2), "GB_s": round(b / (t_ms / 1e3 / cnt) / 1e9, 1)}
+    demag_ms = sum(ktimes[k][0] for k in ("xfwd", "yfwd", "zconv", "yinv", "xinv"))
+    demag_bytes = sum(algorithmic_bytes(k, n, s) for k in ("xfwd", "yfwd", "zconv", "yinv", "xinv"))
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        pinned = torch.from_numpy(m_host.astype(np.float64 if prec == mm.MM_F64 else np.float32)).pin_memory()
+        out = torch.empty_like(pinned).pin_memory()
+        mm.mm_enable_kernel_timing(ctx, True)
+        t_s, dt_s = 0.0, 1e-14
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        trials = 0
+        for _ in range(args.e2e_steps):
+            m.copy_(pinned, non_blocking=True)
+            t_s, dt_s, _ = mm.mm_llg_step(ctx, m, t_s, dt_s, mm.MM_RKF45, 1e-5)
+            out.copy_(m)
+            a_, r_, _, _ = mm.mm_step_stats(ctx)
+            trials += a_ + r_
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        mm.mm_enable_kernel_timing(ctx, False)
+        e2e = {"value": 6 * trials / el * world, "unit": UNIT, "h2d_bytes_per_step": int(pinned.numel() * pinned.element_size()),
+               "d2h_bytes_per_step": int(out.numel() * out.element_size()),
+               "steps": args.e2e_steps, "api": "mm_llg_step (RKF45) per step, m copied host->device before and "
+                                                "device->host after every step"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, m_host)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / max(accepted, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": "film512: 512x512x16 cells of 2 nm (padded FFT 1024x1024x32), Ms 8e5 A/m, "
+                                   "A 1.3e-11 J/m, alpha 0.5, seeded vortex + 5% noise, adaptive RKF45 tol 1e-5 "
+                                   "via relax()",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "no flush: one field evaluation moves ~1.9 GB, far above the 129 MB L2"},
+            "llg_mcell_steps_per_s": mcell,
+            "accepted_steps": accepted, "rejected_trials": rejected, "field_evals": evals,
+            "demag_ms_per_eval": demag_ms / max(evals, 1),
+            "demag_GB_s": demag_bytes / (demag_ms / 1e3 / max(evals, 1)) / 1e9,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_source": f"{peak_src} (hbm_gbs)",
+                         "algorithmic_bytes_per_launch": algo},
+            "kernels": per_kernel, "kernel_time_share": kernel_share,
+            "clocks": clk, "e2e": e2e, "gpu_launches": launches, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    mm.mm_destroy(ctx)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,182 @@
+/*
+ * mm.h - C ABI of the GB300 micromagnetic hot-path library (libmm_gb300.so).
+ *
+ * The library evaluates the finite-difference micromagnetic effective field
+ * and integrates the Landau-Lifshitz-Gilbert equation on one NVIDIA GB300
+ * (sm_103a):
+ *   - demagnetisation field: the zero-padded FFT convolution of M = Ms m with
+ *     the Newell tensor (paper, Implementation section, Eq. 4 and the
+ *     paragraph after it; Newell's formulas are cited there, not printed);
+ *   - exchange field (Eq. 2), read for the unit magnetisation m;
+ *   - uniaxial anisotropy and a uniform Zeeman field (named in the
+ *     Implementation section as local fields);
+ *   - the LLG right-hand side (Eq. 1) for unit m, advanced with classic RK4 or
+ *     Fehlberg's adaptive RKF45 (the paper's integrator, Implementation
+ *     section, paragraph on ODE solvers);
+ *   - energies and the maximum torque, and relax() built on RKF45.
+ *
+ * Conventions shared by every entry point
+ *   - Units are SI: lengths in m, Ms and fields in A/m, A in J/m, Ku in J/m^3,
+ *     time in s, energies in J.
+ *   - Vector fields (m, H) are component-planar arrays [3][nz][ny][nx] with x
+ *     fastest: component c of cell (x, y, z) sits at
+ *     c*N + (z*ny + y)*nx + x, N = nx*ny*nz.  Scalar fields are [nz][ny][nx].
+ *   - Element type is the context's precision: float for MM_F32, double for
+ *     MM_F64.  Pointers named "device" must be device memory of the current
+ *     CUDA device, 256-byte aligned (what cudaMalloc and torch give), owned by
+ *     the caller, never freed or retained by the library.
+ *   - Work is enqueued on the stream given at mm_init_mesh (or mm_set_stream).
+ *     Calls that return host scalars (energies, torque, step errors) wait for
+ *     that stream.  Calls on one context must not overlap on the host.
+ *   - Mesh sizes: each of nx, ny, nz is 1 or a power of two up to 512.
+ *   - Every function returns MM_OK (0) or a negative MM_ERR_* code;
+ *     mm_last_error() then describes the failure.  A failed call leaves the
+ *     caller's buffers in an unspecified state but the context usable, except
+ *     after MM_ERR_CUDA, which reports a CUDA error of the device context.
+ */
+#ifndef MM_GB300_H
+#define MM_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mm_ctx mm_ctx;
+
+enum { MM_F32 = 0, MM_F64 = 1 };
+enum { MM_RK4 = 0, MM_RKF45 = 1 };
+
+enum {
+    MM_OK = 0,
+    MM_ERR_INVALID_ARG = -1,  /* bad size, spacing, material value or null pointer */
+    MM_ERR_CUDA = -2,         /* a CUDA call failed (text in mm_last_error) */
+    MM_ERR_NONFINITE = -3,    /* NaN or Inf met in m or in a step's result */
+    MM_ERR_DT_UNDERFLOW = -4, /* RKF45 shrank dt below the floor (1e-20 s) */
+    MM_ERR_NOT_CONVERGED = -5,/* relax() hit max_steps before torque or t_max */
+    MM_ERR_TIMEOUT = -6,      /* a bounded device wait gave up */
+    MM_ERR_NOMEM = -7         /* device allocation failed in mm_init_mesh */
+};
+
+/* Create a context for an nx x ny x nz mesh of dx x dy x dz cells.
+ * Computes the Newell tensor on the device (double-double arithmetic),
+ * transforms it and keeps its real k-space octant at the path precision;
+ * allocates every scratch buffer the hot path needs (no allocation happens
+ * after this call).  Material defaults: Ms = 8e5, A = 1.3e-11, alpha = 0.02,
+ * Ku = 0, u = z, no external field.
+ *   out        receives the context (host pointer to a host pointer)
+ *   precision  MM_F32 or MM_F64
+ *   stream     cudaStream_t to enqueue on (NULL = legacy default stream of
+ *              the CUDA runtime's current device); the context lives on the
+ *              stream's device and selects it at every call
+ * Errors: INVALID_ARG (sizes, spacing <= 0, out NULL), NOMEM, CUDA. */
+int mm_init_mesh(mm_ctx** out, int nx, int ny, int nz, double dx, double dy, double dz,
+                 int precision, void* stream);
+
+/* Change the stream later calls enqueue on (it must be on the context's
+ * device; INVALID_ARG otherwise). */
+int mm_set_stream(mm_ctx* ctx, void* stream);
+
+/* Uniform material (Eq. 1 and 2 parameters plus anisotropy).  u_anis may be
+ * NULL (then z); it is normalised.  Errors: INVALID_ARG for Ms < 0, A < 0,
+ * alpha < 0, a zero u_anis. */
+int mm_set_material(mm_ctx* ctx, double Ms, double A, double alpha, double Ku,
+                    const double u_anis[3]);
+
+/* Per-cell Ms and/or A ([nz][ny][nx] device arrays of the path precision);
+ * NULL keeps the uniform value.  The arrays are copied; Ms = 0 marks vacuum
+ * cells (no field, no motion, skipped as exchange neighbours). */
+int mm_set_material_fields(mm_ctx* ctx, const void* Ms_cell, const void* A_cell);
+
+/* Uniform external (Zeeman) field in A/m. */
+int mm_set_external_field(mm_ctx* ctx, double hx, double hy, double hz);
+
+/* H = demagnetisation field of m (Eq. 4), both device [3][nz][ny][nx]. */
+int mm_demag_field(mm_ctx* ctx, const void* m, void* H);
+
+/* H = exchange field of m (Eq. 2), 6-point stencil, harmonic-mean A,
+ * free boundary; device [3][nz][ny][nx]. */
+int mm_exchange_field(mm_ctx* ctx, const void* m, void* H);
+
+/* H = demag + exchange + anisotropy + Zeeman (at vacuum cells only the
+ * demag stray field). */
+int mm_effective_field(mm_ctx* ctx, const void* m, void* H);
+
+/* One LLG step of m in place (device [3][nz][ny][nx]).
+ *   method MM_RK4: fixed step *dt; *t += *dt; *err_out (nullable) = 0.
+ *   method MM_RKF45: trial steps from *dt until the embedded error
+ *     max_cells |m5 - m4| <= tol; on return *t is advanced by the accepted
+ *     step, *dt holds the proposed next step and *err_out the accepted error.
+ * m is renormalised after the step.  Errors: INVALID_ARG, NONFINITE,
+ * DT_UNDERFLOW, CUDA. */
+int mm_llg_step(mm_ctx* ctx, void* m, double* t, double* dt, int method, double tol,
+                double* err_out);
+
+/* RKF45 relaxation (tol 1e-5, first dt 1e-14 s) until
+ * max_cells |m x H_eff| / Ms <= torque_tol (checked every 10 steps) or the
+ * time reaches t_max.  *t_out, *steps_out (nullable) receive the simulated
+ * time and accepted step count.  Step-size control stays on the device.
+ * Errors: NOT_CONVERGED when max_steps is reached first, NONFINITE,
+ * DT_UNDERFLOW, CUDA. */
+int mm_relax(mm_ctx* ctx, void* m, double t_max, double torque_tol, long max_steps,
+             double* t_out, long* steps_out);
+
+/* E_out[0..3] = demag, exchange, anisotropy, Zeeman energy of m in J
+ * (float64 accumulation on the device). */
+int mm_energy(mm_ctx* ctx, const void* m, double E_out[4]);
+
+/* *out = max over magnetic cells of |m x H_eff| / Ms. */
+int mm_max_torque(mm_ctx* ctx, const void* m, double* out);
+
+/* Real-space Newell tensor the context computed: host double array
+ * [6][nz][ny][nx] for the non-negative offsets (i, j, k), components
+ * xx, yy, zz, xy, xz, yz (negative offsets follow by parity). */
+int mm_newell_tensor(mm_ctx* ctx, double* host_out);
+
+/* Save m (device) with t and dt to a binary file; load it back into m.
+ * The file records nx, ny, nz and the precision and is rejected on mismatch. */
+int mm_save_state(mm_ctx* ctx, const void* m, double t, double dt, const char* path);
+int mm_load_state(mm_ctx* ctx, void* m, double* t, double* dt, const char* path);
+
+/* Free the context and everything it allocated.  NULL is a no-op. */
+void mm_destroy(mm_ctx* ctx);
+
+/* Text of the last failure on this context ("" if none).  Valid until the
+ * next call on the context.  With ctx NULL: the last mm_init_mesh failure. */
+const char* mm_last_error(const mm_ctx* ctx);
+
+/* Number of kernels this context has launched since creation (all entry
+ * points), for launch accounting. */
+long mm_kernel_launches(const mm_ctx* ctx);
+
+/* Kernel classes for per-kernel timing. */
+enum {
+    MM_K_XFWD = 0,   /* demag pass 1: x real-to-complex, pruned          */
+    MM_K_YFWD = 1,   /* demag pass 2: y forward, pruned input             */
+    MM_K_ZCONV = 2,  /* demag pass 3: z forward, tensor product, z inverse */
+    MM_K_YINV = 3,   /* demag pass 4: y inverse, pruned output            */
+    MM_K_XINV = 4,   /* demag pass 5: x complex-to-real, pruned output    */
+    MM_K_STAGE = 5,  /* fused exchange + local fields + LLG + RK stage    */
+    MM_K_CONTROL = 6,/* RKF45 controller and commit                       */
+    MM_K_REDUCE = 7, /* energies, torque, finiteness check, field kernels */
+    MM_K_COUNT = 8
+};
+
+/* Turn per-kernel timing on (1) or off (0).  When on, every launch of the
+ * context is bracketed by CUDA events recorded on the context's stream.
+ * Turning it on clears the accumulated times. */
+int mm_enable_kernel_timing(mm_ctx* ctx, int enable);
+
+/* Waits for the stream, then reports the summed device time (ms) and the
+ * launch count of kernel class `kernel` since timing was enabled. */
+int mm_kernel_time(mm_ctx* ctx, int kernel, double* total_ms, long* launches);
+
+/* After any call that waited for the stream (llg_step, relax, energy,
+ * torque): accepted steps, rejected RKF45 trials, time and next dt of the
+ * last integration call.  Any pointer may be NULL. */
+int mm_step_stats(const mm_ctx* ctx, long* accepted, long* rejected, double* t, double* dt);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MM_GB300_H */

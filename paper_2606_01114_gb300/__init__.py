@@ -1,0 +1,277 @@
+"""Python binding of libmm_gb300.so, the GB300 micromagnetic hot-path library.
+
+Argument marshalling only: every function forwards to the C entry point of
+the same name in ``include/mm.h`` and raises ``MMError`` on a non-zero return
+code.  Device arrays are torch CUDA tensors (or any object with ``data_ptr``,
+``is_cuda``, ``dtype``, ``shape`` and ``is_contiguous``), vector fields shaped
+(3, nz, ny, nx), scalars (nz, ny, nx), dtype float32 for MM_F32 contexts and
+float64 for MM_F64.  All compute happens in the library's CUDA kernels; if
+the library is not built, loading fails loudly.
+
+Conversions from the paper's (nx, ny, nz, 3) layout: ``from_paper_layout`` /
+``to_paper_layout``.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+MM_F32, MM_F64 = 0, 1
+MM_RK4, MM_RKF45 = 0, 1
+MM_OK = 0
+MM_ERR_INVALID_ARG = -1
+MM_ERR_CUDA = -2
+MM_ERR_NONFINITE = -3
+MM_ERR_DT_UNDERFLOW = -4
+MM_ERR_NOT_CONVERGED = -5
+MM_ERR_TIMEOUT = -6
+MM_ERR_NOMEM = -7
+# kernel classes for mm_kernel_time
+MM_K_XFWD, MM_K_YFWD, MM_K_ZCONV, MM_K_YINV, MM_K_XINV, MM_K_STAGE, MM_K_CONTROL, MM_K_REDUCE = range(8)
+MM_K_COUNT = 8
+KERNEL_NAMES = ("xfwd", "yfwd", "zconv", "yinv", "xinv", "stage", "control", "reduce")
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmm_gb300.so")
+_lib = None
+
+
+class MMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2606_01114_gb300.build` "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_long
+    DP = ctypes.POINTER(ctypes.c_double)
+    LP = ctypes.POINTER(ctypes.c_long)
+    sig = {
+        "mm_init_mesh": (I, [ctypes.POINTER(P), I, I, I, D, D, D, I, P]),
+        "mm_set_stream": (I, [P, P]),
+        "mm_set_material": (I, [P, D, D, D, D, DP]),
+        "mm_set_material_fields": (I, [P, P, P]),
+        "mm_set_external_field": (I, [P, D, D, D]),
+        "mm_demag_field": (I, [P, P, P]),
+        "mm_exchange_field": (I, [P, P, P]),
+        "mm_effective_field": (I, [P, P, P]),
+        "mm_llg_step": (I, [P, P, DP, DP, I, D, DP]),
+        "mm_relax": (I, [P, P, D, D, L, DP, LP]),
+        "mm_energy": (I, [P, P, DP]),
+        "mm_max_torque": (I, [P, P, DP]),
+        "mm_newell_tensor": (I, [P, DP]),
+        "mm_save_state": (I, [P, P, D, D, ctypes.c_char_p]),
+        "mm_load_state": (I, [P, P, DP, DP, ctypes.c_char_p]),
+        "mm_destroy": (None, [P]),
+        "mm_last_error": (ctypes.c_char_p, [P]),
+        "mm_kernel_launches": (L, [P]),
+        "mm_enable_kernel_timing": (I, [P, I]),
+        "mm_kernel_time": (I, [P, I, DP, LP]),
+        "mm_step_stats": (I, [P, LP, LP, DP, DP]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class Context:
+    """Handle returned by ``mm_init_mesh``: the C context plus its shape."""
+
+    def __init__(self, handle, n, d, precision):
+        self.handle = handle
+        self.n = tuple(n)
+        self.d = tuple(d)
+        self.precision = precision
+
+    @property
+    def shape3(self):
+        nx, ny, nz = self.n
+        return (3, nz, ny, nx)
+
+    @property
+    def shape1(self):
+        nx, ny, nz = self.n
+        return (nz, ny, nx)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.mm_destroy(self.handle)
+            self.handle = None
+
+
+def _check(ctx, rc):
+    if rc != MM_OK:
+        h = ctx.handle if isinstance(ctx, Context) else None
+        raise MMError(rc, _load().mm_last_error(h).decode())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:  # pragma: no cover
+            pass
+        return ctypes.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dev(ctx, t, shape, name):
+    if t is None:
+        return None
+    want = "float64" if ctx.precision == MM_F64 else "float32"
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if str(t.dtype).split(".")[-1] != want:
+        raise ValueError(f"{name} must be {want} for this context, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {shape}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def mm_init_mesh(nx, ny, nz, dx, dy, dz, precision=MM_F32, stream=None):
+    lib = _load()
+    h = ctypes.c_void_p()
+    rc = lib.mm_init_mesh(ctypes.byref(h), int(nx), int(ny), int(nz), float(dx), float(dy), float(dz),
+                          int(precision), _stream_ptr(stream))
+    if rc != MM_OK:
+        raise MMError(rc, lib.mm_last_error(None).decode())
+    return Context(h, (nx, ny, nz), (dx, dy, dz), precision)
+
+
+def mm_set_stream(ctx, stream):
+    _check(ctx, _load().mm_set_stream(ctx.handle, _stream_ptr(stream)))
+
+
+def mm_set_material(ctx, Ms, A, alpha, Ku=0.0, u=None):
+    uu = None if u is None else (ctypes.c_double * 3)(*[float(v) for v in u])
+    _check(ctx, _load().mm_set_material(ctx.handle, float(Ms), float(A), float(alpha), float(Ku), uu))
+
+
+def mm_set_material_fields(ctx, Ms_cell=None, A_cell=None):
+    _check(ctx, _load().mm_set_material_fields(ctx.handle, _dev(ctx, Ms_cell, ctx.shape1, "Ms_cell"),
+                                               _dev(ctx, A_cell, ctx.shape1, "A_cell")))
+
+
+def mm_set_external_field(ctx, hx, hy, hz):
+    _check(ctx, _load().mm_set_external_field(ctx.handle, float(hx), float(hy), float(hz)))
+
+
+def mm_demag_field(ctx, m, H):
+    _check(ctx, _load().mm_demag_field(ctx.handle, _dev(ctx, m, ctx.shape3, "m"), _dev(ctx, H, ctx.shape3, "H")))
+
+
+def mm_exchange_field(ctx, m, H):
+    _check(ctx, _load().mm_exchange_field(ctx.handle, _dev(ctx, m, ctx.shape3, "m"), _dev(ctx, H, ctx.shape3, "H")))
+
+
+def mm_effective_field(ctx, m, H):
+    _check(ctx, _load().mm_effective_field(ctx.handle, _dev(ctx, m, ctx.shape3, "m"), _dev(ctx, H, ctx.shape3, "H")))
+
+
+def mm_llg_step(ctx, m, t, dt, method=MM_RK4, tol=1e-5):
+    """Returns (t, dt, err) after one accepted step of m in place."""
+    tt, dd, ee = ctypes.c_double(t), ctypes.c_double(dt), ctypes.c_double(0.0)
+    _check(ctx, _load().mm_llg_step(ctx.handle, _dev(ctx, m, ctx.shape3, "m"), ctypes.byref(tt), ctypes.byref(dd),
+                                     int(method), float(tol), ctypes.byref(ee)))
+    return tt.value, dd.value, ee.value
+
+
+def mm_relax(ctx, m, t_max, torque_tol=1e-4, max_steps=1000000):
+    """Returns (t, accepted_steps)."""
+    tt, ss = ctypes.c_double(0.0), ctypes.c_long(0)
+    _check(ctx, _load().mm_relax(ctx.handle, _dev(ctx, m, ctx.shape3, "m"), float(t_max), float(torque_tol),
+                                 int(max_steps), ctypes.byref(tt), ctypes.byref(ss)))
+    return tt.value, ss.value
+
+
+def mm_energy(ctx, m):
+    E = (ctypes.c_double * 4)()
+    _check(ctx, _load().mm_energy(ctx.handle, _dev(ctx, m, ctx.shape3, "m"), E))
+    return np.array(E[:])
+
+
+def mm_max_torque(ctx, m):
+    out = ctypes.c_double(0.0)
+    _check(ctx, _load().mm_max_torque(ctx.handle, _dev(ctx, m, ctx.shape3, "m"), ctypes.byref(out)))
+    return out.value
+
+
+def mm_newell_tensor(ctx):
+    nx, ny, nz = ctx.n
+    out = np.empty((6, nz, ny, nx), dtype=np.float64)
+    _check(ctx, _load().mm_newell_tensor(ctx.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
+
+
+def mm_save_state(ctx, m, t, dt, path):
+    _check(ctx, _load().mm_save_state(ctx.handle, _dev(ctx, m, ctx.shape3, "m"), float(t), float(dt),
+                                      os.fsencode(path)))
+
+
+def mm_load_state(ctx, m, path):
+    tt, dd = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(ctx, _load().mm_load_state(ctx.handle, _dev(ctx, m, ctx.shape3, "m"), ctypes.byref(tt), ctypes.byref(dd),
+                                      os.fsencode(path)))
+    return tt.value, dd.value
+
+
+def mm_destroy(ctx):
+    if ctx.handle:
+        _load().mm_destroy(ctx.handle)
+        ctx.handle = None
+
+
+def mm_last_error(ctx=None):
+    return _load().mm_last_error(ctx.handle if ctx is not None else None).decode()
+
+
+def mm_kernel_launches(ctx):
+    return int(_load().mm_kernel_launches(ctx.handle))
+
+
+def mm_enable_kernel_timing(ctx, enable=True):
+    _check(ctx, _load().mm_enable_kernel_timing(ctx.handle, 1 if enable else 0))
+
+
+def mm_kernel_time(ctx, kernel):
+    """Returns (total_ms, launches) of kernel class ``kernel`` since timing was enabled."""
+    ms, n = ctypes.c_double(0.0), ctypes.c_long(0)
+    _check(ctx, _load().mm_kernel_time(ctx.handle, int(kernel), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def mm_step_stats(ctx):
+    """Returns (accepted, rejected, t, dt) of the last integration call."""
+    a, r = ctypes.c_long(0), ctypes.c_long(0)
+    t, dt = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(ctx, _load().mm_step_stats(ctx.handle, ctypes.byref(a), ctypes.byref(r), ctypes.byref(t), ctypes.byref(dt)))
+    return a.value, r.value, t.value, dt.value
+
+
+def from_paper_layout(m_xyz3):
+    """(nx, ny, nz, 3) -> (3, nz, ny, nx), the library's component-planar layout."""
+    return m_xyz3.permute(3, 2, 1, 0).contiguous() if hasattr(m_xyz3, "permute") else \
+        np.ascontiguousarray(np.transpose(m_xyz3, (3, 2, 1, 0)))
+
+
+def to_paper_layout(m_3zyx):
+    """(3, nz, ny, nx) -> (nx, ny, nz, 3)."""
+    return m_3zyx.permute(3, 2, 1, 0).contiguous() if hasattr(m_3zyx, "permute") else \
+        np.ascontiguousarray(np.transpose(m_3zyx, (3, 2, 1, 0)))

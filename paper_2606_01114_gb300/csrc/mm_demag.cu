@@ -1,0 +1,453 @@
+// Demagnetisation field as a zero-padded FFT convolution (paper, Implementation
+// section, Eq. 4 and the FFT paragraph after it): H = -N * M, M = Ms m,
+// computed on a grid padded to P = 2n per axis (1 when n = 1), transforms
+// unnormalised, inverse scaled once at the end.
+//
+// Five passes over HBM, each a batched shared-memory FFT (mm_fft.cuh):
+//   K2 x-forward: real rows of M (only the nx non-zero values are read) are
+//      packed two-reals-per-complex into a length Px/2 complex FFT, then
+//      unpacked to the Hx = nx + 1 non-redundant frequencies;
+//   K3 y-forward: columns of Py points of which only ny are non-zero (the
+//      zero half is never read);
+//   K4 z-forward, the 6-component symmetric tensor product with the real
+//      k-space Newell octant, and the z-inverse, fused in one pass; only the
+//      nz un-padded z rows are read and written;
+//   K5 y-inverse keeping ny of the Py outputs;
+//   K6 x-inverse (complex-to-real by the same packing) keeping nx outputs and
+//      applying the scale 1 / ((Px/2) Py Pz).
+// K1 (demag_setup) computes the Newell tensor on the padded real grid in
+// double-double (mm_newell.cu), runs the same passes unpruned in FP64 and
+// keeps the real octant kx <= nx, ky <= Py/2, kz <= Pz/2 at path precision;
+// negative frequencies follow from each component's parity.
+#include <cmath>
+#include <vector>
+
+#include "mm_fft.cuh"
+
+namespace mm {
+namespace {
+
+template <typename T> using C_t = typename cx<T>::type;
+
+// ------------------------------------------------------------------ K2
+// Real rows -> packed complex FFT -> Hx frequencies.
+//   in row r at in + r*in_ld, nin real values (even count, rest zero)
+//   Ms: per-cell array indexed (r mod ms_rows)*in_ld + x, or nullptr (scalar ms)
+template <typename T>
+__global__ void k_xfwd(const T* __restrict__ in, long in_ld, int nin, const T* __restrict__ Ms, T ms,
+                       long ms_rows, C_t<T>* __restrict__ out, int Hs, int L, long rows, int B,
+                       const C_t<T>* __restrict__ twL, const C_t<T>* __restrict__ twP) {
+    using C = C_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* s = reinterpret_cast<C*>(smem_raw);
+    const int se = B + 1;
+    const long r0 = (long)blockIdx.x * B;
+    const int npair = nin / 2;
+    for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x) {
+        int b = idx / L, j = idx % L;
+        long r = r0 + b;
+        C v = cmk<C>(0, 0);
+        if (j < npair && r < rows) {
+            const C* rowp = reinterpret_cast<const C*>(in + r * in_ld);
+            v = rowp[j];
+            if (Ms) {
+                const C* msp = reinterpret_cast<const C*>(Ms + (r % ms_rows) * in_ld);
+                C w = msp[j];
+                v.x *= w.x;
+                v.y *= w.y;
+            } else {
+                v.x *= ms;
+                v.y *= ms;
+            }
+        }
+        s[j * se + b] = v;
+    }
+    __syncthreads();
+    fft_lines<-1>(s, L, B, se, twL);
+    const T half = (T)0.5;
+    for (int idx = threadIdx.x; idx < B * (L + 1); idx += blockDim.x) {
+        int b = idx / (L + 1), k = idx % (L + 1);
+        long r = r0 + b;
+        if (r >= rows) continue;
+        C zk = s[(k % L) * se + b];
+        C zc = cconj(s[((L - k) % L) * se + b]);
+        C e = cscale(cadd(zk, zc), half);
+        C d = cscale(csub(zk, zc), half);
+        // X = E - i w^k D, w = exp(-2 pi i / Px)
+        C wd = cmul(twP[k], d);
+        out[r * Hs + k] = cmk<C>(e.x + wd.y, e.y - wd.x);
+    }
+}
+
+// nx == 1: no x transform, M copied into the complex array.
+template <typename T>
+__global__ void k_x1fwd(const T* __restrict__ in, const T* __restrict__ Ms, T ms, long ms_rows,
+                        C_t<T>* __restrict__ out, int Hs, long rows) {
+    long r = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    T w = Ms ? Ms[r % ms_rows] : ms;
+    out[r * Hs] = cmk<C_t<T>>(in[r] * w, (T)0);
+}
+
+// ------------------------------------------------------------------ K6
+// Hx frequencies -> inverse packed complex FFT -> nx real outputs, scaled.
+template <typename T>
+__global__ void k_xinv(const C_t<T>* __restrict__ in, int Hs, T* __restrict__ out, int nx, int L, long rows,
+                       int B, T scale, const C_t<T>* __restrict__ twL, const C_t<T>* __restrict__ twP) {
+    using C = C_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* s = reinterpret_cast<C*>(smem_raw);
+    const int se = B + 1;
+    const long r0 = (long)blockIdx.x * B;
+    const T half = (T)0.5;
+    for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x) {
+        int b = idx / L, k = idx % L;
+        long r = r0 + b;
+        C z = cmk<C>(0, 0);
+        if (r < rows) {
+            C xk = in[r * Hs + k];
+            C xc = cconj(in[r * Hs + (L - k)]);
+            C e = cscale(cadd(xk, xc), half);
+            C o = cmul(cscale(csub(xk, xc), half), cconj(twP[k]));   // times exp(+2 pi i k / Px)
+            z = cmk<C>(e.x - o.y, e.y + o.x);                          // E + i O
+        }
+        s[k * se + b] = z;
+    }
+    __syncthreads();
+    fft_lines<+1>(s, L, B, se, twL);
+    const int npair = nx / 2;
+    for (int idx = threadIdx.x; idx < B * npair; idx += blockDim.x) {
+        int b = idx / npair, j = idx % npair;
+        long r = r0 + b;
+        if (r >= rows) continue;
+        C z = s[j * se + b];
+        C* op = reinterpret_cast<C*>(out + r * (long)nx);
+        op[j] = cmk<C>(z.x * scale, z.y * scale);
+    }
+}
+
+template <typename T>
+__global__ void k_x1inv(const C_t<T>* __restrict__ in, int Hs, T* __restrict__ out, long rows, T scale) {
+    long r = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    out[r] = in[r * Hs].x * scale;
+}
+
+// ----------------------------------------------------------- K3 / K5
+// Column FFTs along an axis with row stride `rs`: a block takes B adjacent
+// columns (kx) of one plane, loads nin rows (rest zero), transforms length L,
+// stores nout rows.  Plane p: inner index p % n_inner, outer p / n_inner.
+struct ColGeom {
+    long rs_in, rs_out;                // row strides (elements)
+    int n_inner;
+    long in_inner, in_outer, out_inner, out_outer;
+};
+
+template <typename T, int DIR>
+__global__ void k_cols(const C_t<T>* in, C_t<T>* out, int L, int nin, int nout, int Hx, int B, ColGeom g,
+                       const C_t<T>* __restrict__ tw) {
+    using C = C_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* s = reinterpret_cast<C*>(smem_raw);
+    const int se = B + 1;
+    const int col0 = blockIdx.x * B;
+    const int p = blockIdx.y;
+    const int pi = p % g.n_inner, po = p / g.n_inner;
+    const C* ib = in + pi * g.in_inner + po * g.in_outer;
+    C* ob = out + pi * g.out_inner + po * g.out_outer;
+    for (int idx = threadIdx.x; idx < L * B; idx += blockDim.x) {
+        int b = idx % B, r = idx / B;
+        int col = col0 + b;
+        C v = cmk<C>(0, 0);
+        if (r < nin && col < Hx) v = ib[r * g.rs_in + col];
+        s[r * se + b] = v;
+    }
+    __syncthreads();
+    fft_lines<DIR>(s, L, B, se, tw);
+    for (int idx = threadIdx.x; idx < nout * B; idx += blockDim.x) {
+        int b = idx % B, r = idx / B;
+        int col = col0 + b;
+        if (col < Hx) ob[r * g.rs_out + col] = s[r * se + b];
+    }
+}
+
+// ------------------------------------------------------------------ K4
+// Per (ky, tile of B kx): z-FFT of the three components (nz of Pz rows
+// non-zero), H^ = -N^ M^ with the symmetric 3x3 real tensor from the octant
+// (N_xy odd in ky, N_xz odd in kz, N_yz odd in both), z-inverse, keep nz.
+template <typename T>
+__global__ void k_zconv(C_t<T>* buf, const T* __restrict__ kern, int nz, int Pz, int Py, int Hs, int Hx,
+                        int Py2, int Pz2, int B, const C_t<T>* __restrict__ twz) {
+    using C = C_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* s = reinterpret_cast<C*>(smem_raw);
+    const int nl = 3 * B, se = nl + 1;
+    const int col0 = blockIdx.x * B;
+    const int ky = blockIdx.y;
+    const long zstride = (long)Py * Hs;
+    const long cstride = (long)nz * zstride;
+    C* base = buf + (long)ky * Hs + col0;
+    for (int idx = threadIdx.x; idx < Pz * nl; idx += blockDim.x) {
+        int b = idx % B, rest = idx / B;
+        int c = rest % 3, z = rest / 3;
+        C v = cmk<C>(0, 0);
+        if (z < nz && col0 + b < Hx) v = base[c * cstride + z * zstride + b];
+        s[z * se + c * B + b] = v;
+    }
+    __syncthreads();
+    fft_lines<-1>(s, Pz, nl, se, twz);
+    const int kyp = ky <= Py / 2 ? ky : Py - ky;
+    const T sy = ky > Py / 2 ? (T)-1 : (T)1;
+    const long kstride = (long)Pz2 * Py2 * Hs;
+    for (int idx = threadIdx.x; idx < Pz * B; idx += blockDim.x) {
+        int b = idx % B, kz = idx / B;
+        int col = col0 + b;
+        if (col >= Hx) continue;
+        int kzp = kz <= Pz / 2 ? kz : Pz - kz;
+        T sz = kz > Pz / 2 ? (T)-1 : (T)1;
+        long kb = ((long)kzp * Py2 + kyp) * Hs + col;
+        T nxx = kern[kb], nyy = kern[kstride + kb], nzz = kern[2 * kstride + kb];
+        T nxy = sy * kern[3 * kstride + kb];
+        T nxz = sz * kern[4 * kstride + kb];
+        T nyz = sy * sz * kern[5 * kstride + kb];
+        C mx = s[kz * se + b], my = s[kz * se + B + b], mz = s[kz * se + 2 * B + b];
+        C hx = cmk<C>(-(nxx * mx.x + nxy * my.x + nxz * mz.x), -(nxx * mx.y + nxy * my.y + nxz * mz.y));
+        C hy = cmk<C>(-(nxy * mx.x + nyy * my.x + nyz * mz.x), -(nxy * mx.y + nyy * my.y + nyz * mz.y));
+        C hz = cmk<C>(-(nxz * mx.x + nyz * my.x + nzz * mz.x), -(nxz * mx.y + nyz * my.y + nzz * mz.y));
+        s[kz * se + b] = hx;
+        s[kz * se + B + b] = hy;
+        s[kz * se + 2 * B + b] = hz;
+    }
+    __syncthreads();
+    fft_lines<+1>(s, Pz, nl, se, twz);
+    for (int idx = threadIdx.x; idx < nz * nl; idx += blockDim.x) {
+        int b = idx % B, rest = idx / B;
+        int c = rest % 3, z = rest / 3;
+        if (col0 + b < Hx) base[c * cstride + z * zstride + b] = s[z * se + c * B + b];
+    }
+}
+
+// K1 tail: keep the real octant of the transformed component, at precision T.
+template <typename T>
+__global__ void k_extract(const double2* __restrict__ X, int Py, int Hs, int Hx, int Py2, int Pz2,
+                          T* __restrict__ kern) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long total = (long)Pz2 * Py2 * Hs;
+    if (idx >= total) return;
+    int kx = (int)(idx % Hs);
+    int ky = (int)((idx / Hs) % Py2);
+    int kz = (int)(idx / ((long)Hs * Py2));
+    T v = 0;
+    if (kx < Hx) v = (T)X[((long)kz * Py + ky) * Hs + kx].x;
+    kern[idx] = v;
+}
+
+// ------------------------------------------------------------ launch helpers
+inline int block_threads(int nact) {
+    int t = nact < 64 ? 64 : nact;
+    t = (t + 31) / 32 * 32;
+    return t > 1024 ? 1024 : t;
+}
+
+inline int pow2_floor(int v) {
+    int p = 1;
+    while (p * 2 <= v) p *= 2;
+    return p;
+}
+
+// lines per block for a transform of length L of complex elements of size cs
+inline int lines_per_block(int L, int cs, int extra_factor) {
+    // active threads nlines*L/8 <= 1024, shared memory <= 64 KiB, at most 64
+    int by_threads = 8192 / (L * extra_factor);
+    int by_smem = 65536 / (L * cs * extra_factor);
+    int b = by_threads < by_smem ? by_threads : by_smem;
+    if (b > 64) b = 64;
+    if (b < 1) b = 1;
+    b = pow2_floor(b);
+    if (L * extra_factor < 8 && b < 8) b = 8;   // nlines*L must be a multiple of 8
+    return b;
+}
+
+template <typename T> const C_t<T>* table(const mm_ctx* ctx, long off);
+template <> const double2* table<double>(const mm_ctx* ctx, long off) { return (const double2*)ctx->tw.f64 + off; }
+template <> const float2* table<float>(const mm_ctx* ctx, long off) { return (const float2*)ctx->tw.f32 + off; }
+
+template <typename T>
+int set_smem(mm_ctx* ctx, const void* fn, size_t bytes) {
+    if (bytes > 48 * 1024) {
+        MM_CUDA_CHECK(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    }
+    return MM_OK;
+}
+
+// x-forward over `rows` rows
+template <typename T>
+int run_xfwd(mm_ctx* ctx, const T* in, long in_ld, int nin, const T* Ms, T ms, long ms_rows, C_t<T>* out,
+             long rows, const C_t<T>* twL, const C_t<T>* twP, int Px) {
+    KernelTimer kt(ctx, MM_K_XFWD);
+    if (Px == 1) {
+        k_x1fwd<T><<<(unsigned)((rows + 255) / 256), 256, 0, ctx->stream>>>(in, Ms, ms, ms_rows, out, ctx->Hs, rows);
+        MM_LAUNCH_CHECK(ctx);
+        return MM_OK;
+    }
+    const int L = Px / 2;
+    const int B = lines_per_block(L, sizeof(C_t<T>), 1);
+    size_t smem = (size_t)L * (B + 1) * sizeof(C_t<T>);
+    int rc = set_smem<T>(ctx, (const void*)k_xfwd<T>, smem);
+    if (rc) return rc;
+    k_xfwd<T><<<(unsigned)((rows + B - 1) / B), block_threads(B * L / 8), smem, ctx->stream>>>(
+        in, in_ld, nin, Ms, ms, ms_rows, out, ctx->Hs, L, rows, B, twL, twP);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+
+template <typename T, int DIR>
+int run_cols(mm_ctx* ctx, const C_t<T>* in, C_t<T>* out, int L, int nin, int nout, int nplanes, ColGeom g,
+             const C_t<T>* tw) {
+    KernelTimer kt(ctx, DIR < 0 ? MM_K_YFWD : MM_K_YINV);
+    const int B = lines_per_block(L, sizeof(C_t<T>), 1);
+    size_t smem = (size_t)L * (B + 1) * sizeof(C_t<T>);
+    int rc = set_smem<T>(ctx, (const void*)k_cols<T, DIR>, smem);
+    if (rc) return rc;
+    dim3 grid((unsigned)((ctx->Hx + B - 1) / B), (unsigned)nplanes);
+    k_cols<T, DIR><<<grid, block_threads(B * L / 8), smem, ctx->stream>>>(in, out, L, nin, nout, ctx->Hx, B, g, tw);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+
+template <typename T>
+int apply(mm_ctx* ctx, const T* m, T* H) {
+    using C = C_t<T>;
+    const long plane = (long)ctx->ny * ctx->nx;
+    const long rows = 3L * ctx->nz * ctx->ny;
+    C* A = (C*)ctx->bufA;
+    C* Bf = (C*)ctx->bufB;
+    C* xout = ctx->Py == 1 ? Bf : A;
+    const T* Ms = ctx->has_Ms_cell ? (const T*)ctx->Ms_cell : nullptr;
+    int rc;
+    // K2
+    rc = run_xfwd<T>(ctx, m, ctx->nx, ctx->nx, Ms, (T)ctx->Ms, (long)ctx->nz * ctx->ny, xout, rows,
+                     table<T>(ctx, ctx->tw.off_lx), table<T>(ctx, ctx->tw.off_px), ctx->Px);
+    if (rc) return rc;
+    (void)plane;
+    // K3
+    if (ctx->Py > 1) {
+        ColGeom g{ctx->Hs, ctx->Hs, 3 * ctx->nz, (long)ctx->ny * ctx->Hs, 0, (long)ctx->Py * ctx->Hs, 0};
+        rc = run_cols<T, -1>(ctx, A, Bf, ctx->Py, ctx->ny, ctx->Py, 3 * ctx->nz, g, table<T>(ctx, ctx->tw.off_py));
+        if (rc) return rc;
+    }
+    // K4
+    {
+        KernelTimer kt(ctx, MM_K_ZCONV);
+        const int Pz = ctx->Pz;
+        int B = Pz >= 8 ? lines_per_block(Pz, sizeof(C), 3) : 16;
+        if (B > 16) B = 16;
+        size_t smem = (size_t)Pz * (3 * B + 1) * sizeof(C);
+        rc = set_smem<T>(ctx, (const void*)k_zconv<T>, smem);
+        if (rc) return rc;
+        dim3 grid((unsigned)((ctx->Hx + B - 1) / B), (unsigned)ctx->Py);
+        k_zconv<T><<<grid, block_threads(3 * B * Pz / 8), smem, ctx->stream>>>(
+            Bf, (const T*)ctx->kern, ctx->nz, Pz, ctx->Py, ctx->Hs, ctx->Hx, ctx->Py2, ctx->Pz2, B,
+            table<T>(ctx, ctx->tw.off_pz));
+        MM_LAUNCH_CHECK(ctx);
+    }
+    // K5
+    if (ctx->Py > 1) {
+        ColGeom g{ctx->Hs, ctx->Hs, 3 * ctx->nz, (long)ctx->Py * ctx->Hs, 0, (long)ctx->ny * ctx->Hs, 0};
+        rc = run_cols<T, +1>(ctx, Bf, A, ctx->Py, ctx->Py, ctx->ny, 3 * ctx->nz, g, table<T>(ctx, ctx->tw.off_py));
+        if (rc) return rc;
+    }
+    // K6
+    const C* xin = ctx->Py == 1 ? Bf : A;
+    const T scale = (T)(1.0 / ((double)ctx->Lx * ctx->Py * ctx->Pz));
+    KernelTimer kt(ctx, MM_K_XINV);
+    if (ctx->Px == 1) {
+        k_x1inv<T><<<(unsigned)((rows + 255) / 256), 256, 0, ctx->stream>>>(xin, ctx->Hs, H, rows, scale);
+        MM_LAUNCH_CHECK(ctx);
+    } else {
+        const int L = ctx->Lx;
+        const int B = lines_per_block(L, sizeof(C), 1);
+        size_t smem = (size_t)L * (B + 1) * sizeof(C);
+        rc = set_smem<T>(ctx, (const void*)k_xinv<T>, smem);
+        if (rc) return rc;
+        k_xinv<T><<<(unsigned)((rows + B - 1) / B), block_threads(B * L / 8), smem, ctx->stream>>>(
+            xin, ctx->Hs, H, ctx->nx, L, rows, B, scale, table<T>(ctx, ctx->tw.off_lx), table<T>(ctx, ctx->tw.off_px));
+        MM_LAUNCH_CHECK(ctx);
+    }
+    return MM_OK;
+}
+
+template <typename T>
+int setup(mm_ctx* ctx) {
+    const long gsize = (long)ctx->Px * ctx->Py * ctx->Pz;
+    const long csize = (long)ctx->Pz * ctx->Py * ctx->Hs;
+    const long fsize = (long)(ctx->nx + 1) * (ctx->ny + 1) * (ctx->nz + 1);
+    double* grid = nullptr;
+    double2* X = nullptr;
+    double2* fg = nullptr;
+    double* oct = nullptr;
+    int rc = MM_OK;
+    auto cleanup = [&]() {
+        cudaFree(grid);
+        cudaFree(X);
+        cudaFree(fg);
+        cudaFree(oct);
+    };
+    if (cudaMalloc(&grid, sizeof(double) * gsize) != cudaSuccess || cudaMalloc(&X, sizeof(double2) * csize) != cudaSuccess ||
+        cudaMalloc(&fg, sizeof(double2) * fsize) != cudaSuccess || cudaMalloc(&oct, sizeof(double) * 6 * ctx->N) != cudaSuccess) {
+        cleanup();
+        cudaGetLastError();
+        return fail(ctx, MM_ERR_NOMEM, "device allocation for the Newell setup failed");
+    }
+    const double2* twL = table<double>(ctx, ctx->tw.off_lx);
+    const double2* twP = table<double>(ctx, ctx->tw.off_px);
+    const long kcomp = (long)ctx->Pz2 * ctx->Py2 * ctx->Hs;
+    for (int c = 0; c < 6 && rc == MM_OK; ++c) {
+        rc = newell_component(ctx, c, grid, oct + c * ctx->N, fg);
+        if (rc) break;
+        rc = run_xfwd<double>(ctx, grid, ctx->Px, ctx->Px, nullptr, 1.0, 1, X, (long)ctx->Pz * ctx->Py, twL, twP, ctx->Px);
+        if (rc) break;
+        if (ctx->Py > 1) {
+            ColGeom g{ctx->Hs, ctx->Hs, ctx->Pz, (long)ctx->Py * ctx->Hs, 0, (long)ctx->Py * ctx->Hs, 0};
+            rc = run_cols<double, -1>(ctx, X, X, ctx->Py, ctx->Py, ctx->Py, ctx->Pz, g, table<double>(ctx, ctx->tw.off_py));
+            if (rc) break;
+        }
+        if (ctx->Pz > 1) {
+            long rs = (long)ctx->Py * ctx->Hs;
+            ColGeom g{rs, rs, ctx->Py, ctx->Hs, 0, ctx->Hs, 0};
+            rc = run_cols<double, -1>(ctx, X, X, ctx->Pz, ctx->Pz, ctx->Pz, ctx->Py, g, table<double>(ctx, ctx->tw.off_pz));
+            if (rc) break;
+        }
+        long total = kcomp;
+        k_extract<T><<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(X, ctx->Py, ctx->Hs, ctx->Hx, ctx->Py2,
+                                                                               ctx->Pz2, (T*)ctx->kern + c * kcomp);
+        ctx->launches++;
+        if (cudaGetLastError() != cudaSuccess) {
+            rc = fail(ctx, MM_ERR_CUDA, "k_extract launch failed");
+            break;
+        }
+    }
+    if (rc == MM_OK) {
+        cudaError_t e = cudaMemcpyAsync(ctx->newell_host, oct, sizeof(double) * 6 * ctx->N, cudaMemcpyDeviceToHost,
+                                        ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) rc = fail(ctx, MM_ERR_CUDA, "Newell setup failed: %s", cudaGetErrorString(e));
+    } else {
+        cudaStreamSynchronize(ctx->stream);
+    }
+    cleanup();
+    return rc;
+}
+
+}  // namespace
+
+int demag_setup(mm_ctx* ctx) {
+    return ctx->prec == MM_F64 ? setup<double>(ctx) : setup<float>(ctx);
+}
+
+int demag_apply(mm_ctx* ctx, const void* m, void* H) {
+    if (ctx->prec == MM_F64) return apply<double>(ctx, (const double*)m, (double*)H);
+    return apply<float>(ctx, (const float*)m, (float*)H);
+}
+
+}  // namespace mm

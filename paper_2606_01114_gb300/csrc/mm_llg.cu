@@ -1,0 +1,537 @@
+// Local part of the effective field and the LLG time step (paper,
+// Implementation section, Eq. 1 and Eq. 2; RKF45 paragraph).
+//
+//   exchange (Eq. 2, unit m):  H_i = 2 / (mu0 Ms_i) sum_nb A_h (m_nb - m_i) / d^2,
+//       A_h = 2 A_i A_nb / (A_i + A_nb), free boundary, Ms = 0 cells are
+//       vacuum (no field, skipped as neighbours);
+//   anisotropy  H = 2 Ku / (mu0 Ms) (m.u) u,   Zeeman H = H_ext;
+//   LLG (Eq. 1, unit m):  dm/dt = -gamma / (1 + alpha^2) [m x H + alpha m x (m x H)].
+//
+// K7 (k_stage) fuses, for one Runge-Kutta stage, the exchange stencil, the
+// local fields, the sum with the demag field of the stage state, the LLG
+// right-hand side and the stage sum of the next trial state, in one pass
+// over HBM.  Its last-stage instance also forms the new state
+// (4th-order solution for RKF45), the embedded error max |m5 - m4| (block
+// reduction + one atomic max per block) and the renormalisation.  The RKF45
+// step control (k_controller) runs on the device, so a step needs no host
+// synchronisation.  Energies and the torque maximum (K9) accumulate in FP64.
+#include <cmath>
+
+#include "mm_internal.cuh"
+
+namespace mm {
+namespace {
+
+// ---------------------------------------------------- Butcher tableaux
+// classic RK4 and Fehlberg's RKF45 (4th-order weights propagated)
+__host__ __device__ constexpr double rk_a(int method, int i, int j) {
+    if (method == MM_RK4) {
+        if (i == 1 && j == 0) return 0.5;
+        if (i == 2 && j == 1) return 0.5;
+        if (i == 3 && j == 2) return 1.0;
+        return 0.0;
+    }
+    switch (i * 8 + j) {
+        case 1 * 8 + 0: return 1.0 / 4.0;
+        case 2 * 8 + 0: return 3.0 / 32.0;
+        case 2 * 8 + 1: return 9.0 / 32.0;
+        case 3 * 8 + 0: return 1932.0 / 2197.0;
+        case 3 * 8 + 1: return -7200.0 / 2197.0;
+        case 3 * 8 + 2: return 7296.0 / 2197.0;
+        case 4 * 8 + 0: return 439.0 / 216.0;
+        case 4 * 8 + 1: return -8.0;
+        case 4 * 8 + 2: return 3680.0 / 513.0;
+        case 4 * 8 + 3: return -845.0 / 4104.0;
+        case 5 * 8 + 0: return -8.0 / 27.0;
+        case 5 * 8 + 1: return 2.0;
+        case 5 * 8 + 2: return -3544.0 / 2565.0;
+        case 5 * 8 + 3: return 1859.0 / 4104.0;
+        case 5 * 8 + 4: return -11.0 / 40.0;
+        default: return 0.0;
+    }
+}
+__host__ __device__ constexpr double rk_b(int method, int j) {
+    if (method == MM_RK4) {
+        return j == 0 ? 1.0 / 6.0 : j == 1 ? 1.0 / 3.0 : j == 2 ? 1.0 / 3.0 : j == 3 ? 1.0 / 6.0 : 0.0;
+    }
+    return j == 0 ? 25.0 / 216.0 : j == 2 ? 1408.0 / 2565.0 : j == 3 ? 2197.0 / 4104.0 : j == 4 ? -1.0 / 5.0 : 0.0;
+}
+// b5 - b4 (RKF45 error weights)
+__host__ __device__ constexpr double rk_e(int method, int j) {
+    if (method == MM_RK4) return 0.0;
+    constexpr double b5[6] = {16.0 / 135.0, 0.0, 6656.0 / 12825.0, 28561.0 / 56430.0, -9.0 / 50.0, 2.0 / 55.0};
+    return b5[j] - rk_b(method, j);
+}
+__host__ __device__ constexpr int rk_stages(int method) { return method == MM_RK4 ? 4 : 6; }
+
+// --------------------------------------------------------- parameters
+template <typename T> struct Params {
+    int nx, ny, nz;
+    long N;
+    const T* Ms_cell;   // nullable
+    const T* A_cell;    // nullable
+    T Ms, A;
+    T cx, cy, cz;       // 2 / (mu0 d^2) per axis
+    T anis;             // 2 Ku / mu0
+    T ux, uy, uz;
+    T hx, hy, hz;
+    T pref;             // -gamma / (1 + alpha^2)
+    T alpha;
+};
+
+template <typename T>
+Params<T> make_params(const mm_ctx* ctx) {
+    Params<T> p;
+    p.nx = ctx->nx;
+    p.ny = ctx->ny;
+    p.nz = ctx->nz;
+    p.N = ctx->N;
+    p.Ms_cell = ctx->has_Ms_cell ? (const T*)ctx->Ms_cell : nullptr;
+    p.A_cell = ctx->has_A_cell ? (const T*)ctx->A_cell : nullptr;
+    p.Ms = (T)ctx->Ms;
+    p.A = (T)ctx->A;
+    p.cx = (T)(2.0 / (kMu0 * ctx->dx * ctx->dx));
+    p.cy = (T)(2.0 / (kMu0 * ctx->dy * ctx->dy));
+    p.cz = (T)(2.0 / (kMu0 * ctx->dz * ctx->dz));
+    p.anis = (T)(2.0 * ctx->Ku / kMu0);
+    p.ux = (T)ctx->u[0];
+    p.uy = (T)ctx->u[1];
+    p.uz = (T)ctx->u[2];
+    p.hx = (T)ctx->hext[0];
+    p.hy = (T)ctx->hext[1];
+    p.hz = (T)ctx->hext[2];
+    p.pref = (T)(-kGamma / (1.0 + ctx->alpha * ctx->alpha));
+    p.alpha = (T)ctx->alpha;
+    return p;
+}
+
+template <typename T> struct V3 { T x, y, z; };
+
+template <typename T>
+__device__ __forceinline__ V3<T> load3(const T* __restrict__ a, long i, long N) {
+    return {a[i], a[i + N], a[i + 2 * N]};
+}
+template <typename T>
+__device__ __forceinline__ void store3(T* __restrict__ a, long i, long N, V3<T> v) {
+    a[i] = v.x;
+    a[i + N] = v.y;
+    a[i + 2 * N] = v.z;
+}
+
+// exchange field at cell i (x, y, z) of state m; Msi > 0
+template <typename T>
+__device__ __forceinline__ V3<T> exchange_at(const Params<T>& p, const T* __restrict__ m, long i, int x, int y,
+                                             int z, V3<T> mi, T Msi) {
+    const T Ai = p.A_cell ? p.A_cell[i] : p.A;
+    T ax = 0, ay = 0, az = 0;
+    auto nb = [&](long j, T c) {
+        T Msj = p.Ms_cell ? p.Ms_cell[j] : p.Ms;
+        if (Msj == (T)0) return;
+        T Ah;
+        if (p.A_cell) {
+            T Aj = p.A_cell[j];
+            T s = Ai + Aj;
+            Ah = s > (T)0 ? (T)2 * Ai * Aj / s : (T)0;
+        } else {
+            Ah = p.A;
+        }
+        T w = Ah * c;
+        ax += w * (m[j] - mi.x);
+        ay += w * (m[j + p.N] - mi.y);
+        az += w * (m[j + 2 * p.N] - mi.z);
+    };
+    const long sx = 1, sy = p.nx, sz = (long)p.nx * p.ny;
+    if (x > 0) nb(i - sx, p.cx);
+    if (x < p.nx - 1) nb(i + sx, p.cx);
+    if (y > 0) nb(i - sy, p.cy);
+    if (y < p.ny - 1) nb(i + sy, p.cy);
+    if (z > 0) nb(i - sz, p.cz);
+    if (z < p.nz - 1) nb(i + sz, p.cz);
+    T inv = (T)1 / Msi;
+    return {ax * inv, ay * inv, az * inv};
+}
+
+// anisotropy + Zeeman at a magnetic cell
+template <typename T>
+__device__ __forceinline__ V3<T> local_at(const Params<T>& p, V3<T> mi, T Msi) {
+    T mu = mi.x * p.ux + mi.y * p.uy + mi.z * p.uz;
+    T k = p.anis / Msi * mu;
+    return {k * p.ux + p.hx, k * p.uy + p.hy, k * p.uz + p.hz};
+}
+
+template <typename T>
+__device__ __forceinline__ V3<T> llg_rhs(const Params<T>& p, V3<T> m, V3<T> H) {
+    V3<T> a = {m.y * H.z - m.z * H.y, m.z * H.x - m.x * H.z, m.x * H.y - m.y * H.x};   // m x H
+    V3<T> b = {m.y * a.z - m.z * a.y, m.z * a.x - m.x * a.z, m.x * a.y - m.y * a.x};   // m x (m x H)
+    return {p.pref * (a.x + p.alpha * b.x), p.pref * (a.y + p.alpha * b.y), p.pref * (a.z + p.alpha * b.z)};
+}
+
+__device__ __forceinline__ void decompose(long i, int nx, int ny, int& x, int& y, int& z) {
+    x = (int)(i % nx);
+    long r = i / nx;
+    y = (int)(r % ny);
+    z = (int)(r / ny);
+}
+
+// block-wide max of a non-negative double, then one atomicMax of its bits
+__device__ __forceinline__ void block_max_atomic(double v, unsigned long long* target) {
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        v = lane < nw ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0 && v > 0.0) atomicMax(target, (unsigned long long)__double_as_longlong(v));
+    }
+}
+
+__device__ __forceinline__ void block_sum_atomic(double v, double* target) {
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        v = lane < nw ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) atomicAdd(target, v);
+    }
+}
+
+// ------------------------------------------------------------- fields
+// mode 0: exchange only; mode 1: Hd + exchange + anisotropy + Zeeman
+template <typename T, int MODE>
+__global__ void k_field(Params<T> p, const T* __restrict__ m, const T* __restrict__ Hd, T* __restrict__ H) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.N) return;
+    int x, y, z;
+    decompose(i, p.nx, p.ny, x, y, z);
+    T Msi = p.Ms_cell ? p.Ms_cell[i] : p.Ms;
+    V3<T> h = {0, 0, 0};
+    if (Msi != (T)0) {
+        V3<T> mi = load3(m, i, p.N);
+        h = exchange_at(p, m, i, x, y, z, mi, Msi);
+        if (MODE == 1) {
+            V3<T> l = local_at(p, mi, Msi);
+            V3<T> d = load3(Hd, i, p.N);
+            h = {h.x + l.x + d.x, h.y + l.y + d.y, h.z + l.z + d.z};
+        }
+    } else if (MODE == 1) {
+        h = load3(Hd, i, p.N);   // vacuum cell: only the stray (demag) field
+    }
+    store3(H, i, p.N, h);
+}
+
+// ------------------------------------------------------------- K7 stage
+template <typename T, int METHOD, int S>
+__global__ void k_stage(Params<T> p, const T* __restrict__ m_in, const T* __restrict__ Hd, const T* m0,
+                        T* const* __restrict__ kbuf, T* m_out, Control* ctl) {
+    constexpr int NS = rk_stages(METHOD);
+    constexpr bool LAST = (S == NS - 1);
+    if (ctl->status != 0 || ctl->done) return;
+    const T dt = (T)ctl->dt;
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    double err = 0.0;
+    if (i < p.N) {
+        int x, y, z;
+        decompose(i, p.nx, p.ny, x, y, z);
+        T Msi = p.Ms_cell ? p.Ms_cell[i] : p.Ms;
+        V3<T> ks = {0, 0, 0};
+        V3<T> mi = load3(m_in, i, p.N);
+        if (Msi != (T)0) {
+            V3<T> h = exchange_at(p, m_in, i, x, y, z, mi, Msi);
+            V3<T> l = local_at(p, mi, Msi);
+            V3<T> d = load3(Hd, i, p.N);
+            h = {h.x + l.x + d.x, h.y + l.y + d.y, h.z + l.z + d.z};
+            ks = llg_rhs(p, mi, h);
+        }
+        V3<T> a0 = S == 0 ? mi : load3(m0, i, p.N);
+        if constexpr (!LAST) {
+            // next trial state m0 + dt sum_j a[S+1][j] k_j
+            V3<T> acc = {0, 0, 0};
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+                const T c = (T)rk_a(METHOD, S + 1, j);
+                if (c != (T)0) {
+                    V3<T> kj = load3(kbuf[j], i, p.N);
+                    acc.x += c * kj.x;
+                    acc.y += c * kj.y;
+                    acc.z += c * kj.z;
+                }
+            }
+            const T cs = (T)rk_a(METHOD, S + 1, S);
+            acc.x += cs * ks.x;
+            acc.y += cs * ks.y;
+            acc.z += cs * ks.z;
+            store3(kbuf[S], i, p.N, ks);
+            store3(m_out, i, p.N, V3<T>{a0.x + dt * acc.x, a0.y + dt * acc.y, a0.z + dt * acc.z});
+        } else {
+            V3<T> acc = {0, 0, 0}, e = {0, 0, 0};
+#pragma unroll
+            for (int j = 0; j < NS; ++j) {
+                const T cb = (T)rk_b(METHOD, j), ce = (T)rk_e(METHOD, j);
+                if (cb != (T)0 || ce != (T)0) {
+                    V3<T> kj = j == S ? ks : load3(kbuf[j], i, p.N);
+                    acc.x += cb * kj.x;
+                    acc.y += cb * kj.y;
+                    acc.z += cb * kj.z;
+                    e.x += ce * kj.x;
+                    e.y += ce * kj.y;
+                    e.z += ce * kj.z;
+                }
+            }
+            V3<T> mn = {a0.x + dt * acc.x, a0.y + dt * acc.y, a0.z + dt * acc.z};
+            T nrm = sqrt(mn.x * mn.x + mn.y * mn.y + mn.z * mn.z);
+            if (Msi != (T)0 && nrm > (T)0) {
+                T inv = (T)1 / nrm;
+                mn = {mn.x * inv, mn.y * inv, mn.z * inv};
+            }
+            const bool bad = !(isfinite((double)mn.x) && isfinite((double)mn.y) && isfinite((double)mn.z));
+            if (METHOD == MM_RKF45) {
+                // a trial that overflowed is rejected (infinite error), as any too-large step
+                err = (double)dt * sqrt((double)e.x * e.x + (double)e.y * e.y + (double)e.z * e.z);
+                if (bad || !isfinite(err)) err = INFINITY;
+            } else if (bad) {
+                atomicCAS(&ctl->status, 0, (int)MM_ERR_NONFINITE);
+            }
+            store3(m_out, i, p.N, mn);
+        }
+    }
+    if constexpr (LAST && METHOD == MM_RKF45) block_max_atomic(err, &ctl->err_bits);
+}
+
+// RKF45 step control on the device.
+__global__ void k_controller(Control* ctl, int method) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (ctl->status != 0 || ctl->done) {
+        ctl->accepted = 0;
+        return;
+    }
+    const double dt = ctl->dt;
+    if (method == MM_RK4) {
+        ctl->accepted = 1;
+        ctl->t += dt;
+        ctl->steps += 1;
+        ctl->dt_next = dt;
+        return;
+    }
+    const double err = __longlong_as_double((long long)ctl->err_bits);
+    const double tol = ctl->tol;
+    const int acc = err <= tol;
+    double fac;
+    if (err <= 0.0) fac = 5.0;
+    else fac = fmin(5.0, fmax(0.2, 0.9 * pow(tol / err, 0.2)));
+    double dtn = dt * fac;
+    ctl->accepted = acc;
+    ctl->err_bits = 0ull;
+    ctl->dt_next = dtn;
+    if (acc) {
+        ctl->t += dt;
+        ctl->steps += 1;
+        ctl->last_err = err;
+    } else {
+        ctl->rejects += 1;
+    }
+    if (dtn < 1e-20) {
+        ctl->status = MM_ERR_DT_UNDERFLOW;
+        return;
+    }
+    double rem = ctl->t_max - ctl->t;
+    if (rem <= 0.0) {
+        ctl->done = 1;
+    } else if (dtn > rem) {
+        dtn = rem;
+    }
+    ctl->dt = dtn;
+}
+
+template <typename T>
+__global__ void k_commit(long n3, const T* __restrict__ src, T* __restrict__ dst, const Control* ctl) {
+    if (!ctl->accepted) return;
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n3) dst[i] = src[i];
+}
+
+// ------------------------------------------------------------- K9
+template <typename T>
+__global__ void k_energy(Params<T> p, const T* __restrict__ m, const T* __restrict__ Hd, double V, double mu0,
+                         double Ku, Control* ctl) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    double ed = 0, ex = 0, ea = 0, ez = 0;
+    if (i < p.N) {
+        int x, y, z;
+        decompose(i, p.nx, p.ny, x, y, z);
+        T Msi = p.Ms_cell ? p.Ms_cell[i] : p.Ms;
+        if (Msi != (T)0) {
+            V3<T> mi = load3(m, i, p.N);
+            V3<T> h = exchange_at(p, m, i, x, y, z, mi, Msi);
+            V3<T> d = load3(Hd, i, p.N);
+            double ms = (double)Msi;
+            ed = -0.5 * mu0 * V * ms * ((double)mi.x * d.x + (double)mi.y * d.y + (double)mi.z * d.z);
+            ex = -0.5 * mu0 * V * ms * ((double)mi.x * h.x + (double)mi.y * h.y + (double)mi.z * h.z);
+            double mu = (double)mi.x * p.ux + (double)mi.y * p.uy + (double)mi.z * p.uz;
+            ea = -Ku * V * mu * mu;
+            ez = -mu0 * V * ms * ((double)mi.x * p.hx + (double)mi.y * p.hy + (double)mi.z * p.hz);
+        }
+    }
+    block_sum_atomic(ed, &ctl->energy[0]);
+    __syncthreads();
+    block_sum_atomic(ex, &ctl->energy[1]);
+    __syncthreads();
+    block_sum_atomic(ea, &ctl->energy[2]);
+    __syncthreads();
+    block_sum_atomic(ez, &ctl->energy[3]);
+}
+
+template <typename T>
+__global__ void k_torque(Params<T> p, const T* __restrict__ m, const T* __restrict__ Hd, Control* ctl) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    double tq = 0.0;
+    if (i < p.N) {
+        int x, y, z;
+        decompose(i, p.nx, p.ny, x, y, z);
+        T Msi = p.Ms_cell ? p.Ms_cell[i] : p.Ms;
+        if (Msi != (T)0) {
+            V3<T> mi = load3(m, i, p.N);
+            V3<T> h = exchange_at(p, m, i, x, y, z, mi, Msi);
+            V3<T> l = local_at(p, mi, Msi);
+            V3<T> d = load3(Hd, i, p.N);
+            double Hx = (double)h.x + l.x + d.x, Hy = (double)h.y + l.y + d.y, Hz = (double)h.z + l.z + d.z;
+            double cx = mi.y * Hz - mi.z * Hy, cy = mi.z * Hx - mi.x * Hz, cz = mi.x * Hy - mi.y * Hx;
+            tq = sqrt(cx * cx + cy * cy + cz * cz) / (double)Msi;
+            if (!isfinite(tq)) tq = 1e300;
+        }
+    }
+    block_max_atomic(tq, &ctl->torque_bits);
+}
+
+template <typename T>
+__global__ void k_finite(long n3, const T* __restrict__ m, Control* ctl) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n3 && !isfinite((double)m[i])) atomicCAS(&ctl->status, 0, (int)MM_ERR_NONFINITE);
+}
+
+constexpr int kThreads = 256;
+inline unsigned blocks_for(long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+template <typename T, int METHOD, int S>
+int launch_stage(mm_ctx* ctx, const Params<T>& p, const void* m_in, const void* m0, void* m_out, T* const* kdev) {
+    KernelTimer kt(ctx, MM_K_STAGE);
+    k_stage<T, METHOD, S><<<blocks_for(p.N), kThreads, 0, ctx->stream>>>(p, (const T*)m_in, (const T*)ctx->Hd,
+                                                                          (const T*)m0, kdev, (T*)m_out, ctx->ctl);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+
+template <typename T, int METHOD>
+int stage_dispatch(mm_ctx* ctx, int s, const void* m_in, const void* m0, void* m_out) {
+    Params<T> p = make_params<T>(ctx);
+    T* const* kdev = (T* const*)ctx->kptrs;
+    switch (s) {
+        case 0: return launch_stage<T, METHOD, 0>(ctx, p, m_in, m0, m_out, kdev);
+        case 1: return launch_stage<T, METHOD, 1>(ctx, p, m_in, m0, m_out, kdev);
+        case 2: return launch_stage<T, METHOD, 2>(ctx, p, m_in, m0, m_out, kdev);
+        case 3: return launch_stage<T, METHOD, 3>(ctx, p, m_in, m0, m_out, kdev);
+        case 4:
+            if constexpr (METHOD == MM_RKF45) return launch_stage<T, METHOD, 4>(ctx, p, m_in, m0, m_out, kdev);
+            break;
+        case 5:
+            if constexpr (METHOD == MM_RKF45) return launch_stage<T, METHOD, 5>(ctx, p, m_in, m0, m_out, kdev);
+            break;
+    }
+    return fail(ctx, MM_ERR_INVALID_ARG, "bad stage %d", s);
+}
+
+template <typename T>
+int exchange_t(mm_ctx* ctx, const void* m, void* H) {
+    KernelTimer kt(ctx, MM_K_REDUCE);
+    Params<T> p = make_params<T>(ctx);
+    k_field<T, 0><<<blocks_for(p.N), kThreads, 0, ctx->stream>>>(p, (const T*)m, nullptr, (T*)H);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+template <typename T>
+int effective_t(mm_ctx* ctx, const void* m, const void* Hd, void* H) {
+    KernelTimer kt(ctx, MM_K_REDUCE);
+    Params<T> p = make_params<T>(ctx);
+    k_field<T, 1><<<blocks_for(p.N), kThreads, 0, ctx->stream>>>(p, (const T*)m, (const T*)Hd, (T*)H);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+template <typename T>
+int energy_t(mm_ctx* ctx, const void* m, const void* Hd) {
+    KernelTimer kt(ctx, MM_K_REDUCE);
+    Params<T> p = make_params<T>(ctx);
+    double V = ctx->dx * ctx->dy * ctx->dz;
+    k_energy<T><<<blocks_for(p.N), kThreads, 0, ctx->stream>>>(p, (const T*)m, (const T*)Hd, V, kMu0, ctx->Ku, ctx->ctl);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+template <typename T>
+int torque_t(mm_ctx* ctx, const void* m, const void* Hd) {
+    KernelTimer kt(ctx, MM_K_REDUCE);
+    Params<T> p = make_params<T>(ctx);
+    k_torque<T><<<blocks_for(p.N), kThreads, 0, ctx->stream>>>(p, (const T*)m, (const T*)Hd, ctx->ctl);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+
+}  // namespace
+
+int field_exchange(mm_ctx* ctx, const void* m, void* H) {
+    return ctx->prec == MM_F64 ? exchange_t<double>(ctx, m, H) : exchange_t<float>(ctx, m, H);
+}
+int field_effective(mm_ctx* ctx, const void* m, const void* Hd, void* H) {
+    return ctx->prec == MM_F64 ? effective_t<double>(ctx, m, Hd, H) : effective_t<float>(ctx, m, Hd, H);
+}
+
+int energy_launch(mm_ctx* ctx, const void* m, const void* Hd) {
+    return ctx->prec == MM_F64 ? energy_t<double>(ctx, m, Hd) : energy_t<float>(ctx, m, Hd);
+}
+int torque_launch(mm_ctx* ctx, const void* m, const void* Hd) {
+    return ctx->prec == MM_F64 ? torque_t<double>(ctx, m, Hd) : torque_t<float>(ctx, m, Hd);
+}
+
+int rk_stage(mm_ctx* ctx, int method, int s, const void* m_in, const void* m0, void* m_out) {
+    if (ctx->prec == MM_F64) {
+        return method == MM_RK4 ? stage_dispatch<double, MM_RK4>(ctx, s, m_in, m0, m_out)
+                                : stage_dispatch<double, MM_RKF45>(ctx, s, m_in, m0, m_out);
+    }
+    return method == MM_RK4 ? stage_dispatch<float, MM_RK4>(ctx, s, m_in, m0, m_out)
+                            : stage_dispatch<float, MM_RKF45>(ctx, s, m_in, m0, m_out);
+}
+
+int rk_controller(mm_ctx* ctx, int method) {
+    KernelTimer kt(ctx, MM_K_CONTROL);
+    k_controller<<<1, 32, 0, ctx->stream>>>(ctx->ctl, method);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+
+int rk_commit(mm_ctx* ctx, void* m0) {
+    KernelTimer kt(ctx, MM_K_CONTROL);
+    long n3 = 3 * ctx->N;
+    if (ctx->prec == MM_F64)
+        k_commit<double><<<blocks_for(n3), kThreads, 0, ctx->stream>>>(n3, (const double*)ctx->mnext, (double*)m0, ctx->ctl);
+    else
+        k_commit<float><<<blocks_for(n3), kThreads, 0, ctx->stream>>>(n3, (const float*)ctx->mnext, (float*)m0, ctx->ctl);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+
+int check_finite_launch(mm_ctx* ctx, const void* m) {
+    KernelTimer kt(ctx, MM_K_REDUCE);
+    long n3 = 3 * ctx->N;
+    if (ctx->prec == MM_F64)
+        k_finite<double><<<blocks_for(n3), kThreads, 0, ctx->stream>>>(n3, (const double*)m, ctx->ctl);
+    else
+        k_finite<float><<<blocks_for(n3), kThreads, 0, ctx->stream>>>(n3, (const float*)m, ctx->ctl);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+
+}  // namespace mm
