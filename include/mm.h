@@ -175,6 +175,33 @@ int mm_kernel_time(mm_ctx* ctx, int kernel, double* total_ms, long* launches);
  * last integration call.  Any pointer may be NULL. */
 int mm_step_stats(const mm_ctx* ctx, long* accepted, long* rejected, double* t, double* dt);
 
+/* Energies without a context and without any device allocation.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory themselves or through this library (for
+ * example code that runs inside a memory pool or arena it does not own, or a
+ * plugin that is handed only its host application's buffers), and so cannot
+ * create a context.  It computes what mm_energy computes (E_out[0..3] =
+ * demag, exchange, anisotropy, Zeeman energy in J) for a uniform material,
+ * taking the demagnetisation field H_demag from the caller (for instance
+ * from mm_demag_field) instead of evaluating it.
+ *   m, H_demag  device arrays [3][nz][ny][nx] of the given precision
+ *   u_anis      anisotropy axis (NULL = z, normalised); h_ext Zeeman field in
+ *               A/m (NULL = none); E_out host array of 4 doubles
+ *   stream      cudaStream_t (NULL = legacy default stream); the call waits
+ *               for it before returning
+ * Scratch: block partial sums live in one fixed array of 1 MiB in the
+ * library's device memory, which every GPU that loads the library keeps
+ * until the process exits.  Meshes above 8,388,608 cells are rejected with
+ * INVALID_ARG.  The call uses no cudaMalloc or cudaFree.  The first call on
+ * each device looks up the array's device address; make that first call
+ * before any stream capture.  All calls share the array, so calls that
+ * overlap on the GPU race and must be serialised by the caller.
+ * Errors (read with mm_last_error(NULL)): INVALID_ARG, CUDA. */
+int mm_energy_noalloc(int nx, int ny, int nz, double dx, double dy, double dz, int precision,
+                      double Ms, double A, double Ku, const double u_anis[3], const double h_ext[3],
+                      const void* m, const void* H_demag, double E_out[4], void* stream);
+
 #ifdef __cplusplus
 }
 #endif

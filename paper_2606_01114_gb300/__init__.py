@@ -76,6 +76,7 @@ def _load():
         "mm_enable_kernel_timing": (I, [P, I]),
         "mm_kernel_time": (I, [P, I, DP, LP]),
         "mm_step_stats": (I, [P, LP, LP, DP, DP]),
+        "mm_energy_noalloc": (I, [I, I, I, D, D, D, I, D, D, D, DP, DP, P, P, DP, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -263,6 +264,29 @@ def mm_step_stats(ctx):
     t, dt = ctypes.c_double(0.0), ctypes.c_double(0.0)
     _check(ctx, _load().mm_step_stats(ctx.handle, ctypes.byref(a), ctypes.byref(r), ctypes.byref(t), ctypes.byref(dt)))
     return a.value, r.value, t.value, dt.value
+
+
+def mm_energy_noalloc(n, d, precision, Ms, A, Ku, u, h_ext, m, H_demag, stream=None):
+    """Energies (demag, exchange, anisotropy, Zeeman) without a context and
+    without any device allocation; H_demag is supplied by the caller.  For
+    callers that cannot allocate device memory (see include/mm.h)."""
+    nx, ny, nz = (int(v) for v in n)
+    want = "float64" if precision == MM_F64 else "float32"
+    for name, t in (("m", m), ("H_demag", H_demag)):
+        if not getattr(t, "is_cuda", False) or str(t.dtype).split(".")[-1] != want:
+            raise ValueError(f"{name} must be a {want} CUDA tensor")
+        if tuple(t.shape) != (3, nz, ny, nx) or not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous with shape {(3, nz, ny, nx)}")
+    uu = None if u is None else (ctypes.c_double * 3)(*[float(v) for v in u])
+    hh = None if h_ext is None else (ctypes.c_double * 3)(*[float(v) for v in h_ext])
+    E = (ctypes.c_double * 4)()
+    lib = _load()
+    rc = lib.mm_energy_noalloc(nx, ny, nz, float(d[0]), float(d[1]), float(d[2]), int(precision), float(Ms),
+                               float(A), float(Ku), uu, hh, ctypes.c_void_p(m.data_ptr()),
+                               ctypes.c_void_p(H_demag.data_ptr()), E, _stream_ptr(stream))
+    if rc != MM_OK:
+        raise MMError(rc, lib.mm_last_error(None).decode())
+    return np.array(E[:])
 
 
 def from_paper_layout(m_xyz3):
