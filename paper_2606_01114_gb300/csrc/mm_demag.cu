@@ -31,28 +31,28 @@ template <typename T> using C_t = typename cx<T>::type;
 
 // ------------------------------------------------------------------ K2
 // Real rows -> packed complex FFT -> Hx frequencies.
-//   in row r at in + r*in_ld, nin real values (even count, rest zero)
-//   Ms: per-cell array indexed (r mod ms_rows)*in_ld + x, or nullptr (scalar ms)
+//   B = 2^lgB rows per block, row r at in + r*in_ld, nin real values (even
+//   count, rest zero); Ms: per-cell array indexed (r mod ms_rows)*in_ld + x,
+//   or nullptr (scalar ms).  Complex length L = 2^lgL = Px / 2.
 template <typename T>
 __global__ void k_xfwd(const T* __restrict__ in, long in_ld, int nin, const T* __restrict__ Ms, T ms,
-                       long ms_rows, C_t<T>* __restrict__ out, int Hs, int L, long rows, int B,
+                       long ms_rows, C_t<T>* __restrict__ out, int Hs, int lgL, long rows, int lgB,
                        const C_t<T>* __restrict__ twL, const C_t<T>* __restrict__ twP) {
     using C = C_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
+    const int L = 1 << lgL, B = 1 << lgB;
     const int se = B + 1;
-    const long r0 = (long)blockIdx.x * B;
-    const int npair = nin / 2;
-    for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x) {
-        int b = idx / L, j = idx % L;
+    const long r0 = (long)blockIdx.x << lgB;
+    const int npair = nin >> 1;
+    for (int idx = threadIdx.x; idx < (B << lgL); idx += blockDim.x) {
+        int b = idx >> lgL, j = idx & (L - 1);
         long r = r0 + b;
         C v = cmk<C>(0, 0);
         if (j < npair && r < rows) {
-            const C* rowp = reinterpret_cast<const C*>(in + r * in_ld);
-            v = rowp[j];
+            v = reinterpret_cast<const C*>(in + r * in_ld)[j];
             if (Ms) {
-                const C* msp = reinterpret_cast<const C*>(Ms + (r % ms_rows) * in_ld);
-                C w = msp[j];
+                C w = reinterpret_cast<const C*>(Ms + (r % ms_rows) * in_ld)[j];
                 v.x *= w.x;
                 v.y *= w.y;
             } else {
@@ -63,17 +63,25 @@ __global__ void k_xfwd(const T* __restrict__ in, long in_ld, int nin, const T* _
         s[j * se + b] = v;
     }
     __syncthreads();
-    fft_lines<-1>(s, L, B, se, twL);
+    const FftGeom g = fft_geom(L, B, 1, se, 0);
+    fft_lines<-1>(s, g, twL);
     const T half = (T)0.5;
-    for (int idx = threadIdx.x; idx < B * (L + 1); idx += blockDim.x) {
-        int b = idx / (L + 1), k = idx % (L + 1);
+    // X_k = E_k - i w^k D_k, E, D the even/odd split of the packed spectrum Z
+    for (int idx = threadIdx.x; idx < (B << lgL) + B; idx += blockDim.x) {
+        int b, k;
+        if (idx < (B << lgL)) {
+            b = idx >> lgL;
+            k = idx & (L - 1);
+        } else {
+            b = idx - (B << lgL);
+            k = L;
+        }
         long r = r0 + b;
         if (r >= rows) continue;
-        C zk = s[(k % L) * se + b];
-        C zc = cconj(s[((L - k) % L) * se + b]);
+        C zk = s[(k & (L - 1)) * se + b];
+        C zc = cconj(s[((L - k) & (L - 1)) * se + b]);
         C e = cscale(cadd(zk, zc), half);
         C d = cscale(csub(zk, zc), half);
-        // X = E - i w^k D, w = exp(-2 pi i / Px)
         C wd = cmul(twP[k], d);
         out[r * Hs + k] = cmk<C>(e.x + wd.y, e.y - wd.x);
     }
@@ -92,16 +100,17 @@ __global__ void k_x1fwd(const T* __restrict__ in, const T* __restrict__ Ms, T ms
 // ------------------------------------------------------------------ K6
 // Hx frequencies -> inverse packed complex FFT -> nx real outputs, scaled.
 template <typename T>
-__global__ void k_xinv(const C_t<T>* __restrict__ in, int Hs, T* __restrict__ out, int nx, int L, long rows,
-                       int B, T scale, const C_t<T>* __restrict__ twL, const C_t<T>* __restrict__ twP) {
+__global__ void k_xinv(const C_t<T>* __restrict__ in, int Hs, T* __restrict__ out, int nx, int lgL, long rows,
+                       int lgB, T scale, const C_t<T>* __restrict__ twL, const C_t<T>* __restrict__ twP) {
     using C = C_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
+    const int L = 1 << lgL, B = 1 << lgB;
     const int se = B + 1;
-    const long r0 = (long)blockIdx.x * B;
+    const long r0 = (long)blockIdx.x << lgB;
     const T half = (T)0.5;
-    for (int idx = threadIdx.x; idx < B * L; idx += blockDim.x) {
-        int b = idx / L, k = idx % L;
+    for (int idx = threadIdx.x; idx < (B << lgL); idx += blockDim.x) {
+        int b = idx >> lgL, k = idx & (L - 1);
         long r = r0 + b;
         C z = cmk<C>(0, 0);
         if (r < rows) {
@@ -114,15 +123,16 @@ __global__ void k_xinv(const C_t<T>* __restrict__ in, int Hs, T* __restrict__ ou
         s[k * se + b] = z;
     }
     __syncthreads();
-    fft_lines<+1>(s, L, B, se, twL);
-    const int npair = nx / 2;
-    for (int idx = threadIdx.x; idx < B * npair; idx += blockDim.x) {
-        int b = idx / npair, j = idx % npair;
+    const FftGeom g = fft_geom(L, B, 1, se, 0);
+    fft_lines<+1>(s, g, twL);
+    const int lgP = ilog2(nx >> 1);
+    const int npair = nx >> 1;
+    for (int idx = threadIdx.x; idx < (B << lgP); idx += blockDim.x) {
+        int b = idx >> lgP, j = idx & (npair - 1);
         long r = r0 + b;
         if (r >= rows) continue;
         C z = s[j * se + b];
-        C* op = reinterpret_cast<C*>(out + r * (long)nx);
-        op[j] = cmk<C>(z.x * scale, z.y * scale);
+        reinterpret_cast<C*>(out + r * (long)nx)[j] = cmk<C>(z.x * scale, z.y * scale);
     }
 }
 
@@ -134,9 +144,10 @@ __global__ void k_x1inv(const C_t<T>* __restrict__ in, int Hs, T* __restrict__ o
 }
 
 // ----------------------------------------------------------- K3 / K5
-// Column FFTs along an axis with row stride `rs`: a block takes B adjacent
-// columns (kx) of one plane, loads nin rows (rest zero), transforms length L,
-// stores nout rows.  Plane p: inner index p % n_inner, outer p / n_inner.
+// Column FFTs along an axis with row stride `rs`: a block takes B = 2^lgB
+// adjacent columns (kx) of one plane, loads nin rows (rest zero), transforms
+// length L = 2^lgL, stores nout rows.  Plane p: inner index p % n_inner,
+// outer p / n_inner.
 struct ColGeom {
     long rs_in, rs_out;                // row strides (elements)
     int n_inner;
@@ -144,28 +155,30 @@ struct ColGeom {
 };
 
 template <typename T, int DIR>
-__global__ void k_cols(const C_t<T>* in, C_t<T>* out, int L, int nin, int nout, int Hx, int B, ColGeom g,
+__global__ void k_cols(const C_t<T>* in, C_t<T>* out, int lgL, int nin, int nout, int Hx, int lgB, ColGeom g,
                        const C_t<T>* __restrict__ tw) {
     using C = C_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
+    const int L = 1 << lgL, B = 1 << lgB;
     const int se = B + 1;
-    const int col0 = blockIdx.x * B;
+    const int col0 = blockIdx.x << lgB;
     const int p = blockIdx.y;
     const int pi = p % g.n_inner, po = p / g.n_inner;
     const C* ib = in + pi * g.in_inner + po * g.in_outer;
     C* ob = out + pi * g.out_inner + po * g.out_outer;
-    for (int idx = threadIdx.x; idx < L * B; idx += blockDim.x) {
-        int b = idx % B, r = idx / B;
+    for (int idx = threadIdx.x; idx < (L << lgB); idx += blockDim.x) {
+        int b = idx & (B - 1), r = idx >> lgB;
         int col = col0 + b;
         C v = cmk<C>(0, 0);
         if (r < nin && col < Hx) v = ib[r * g.rs_in + col];
         s[r * se + b] = v;
     }
     __syncthreads();
-    fft_lines<DIR>(s, L, B, se, tw);
-    for (int idx = threadIdx.x; idx < nout * B; idx += blockDim.x) {
-        int b = idx % B, r = idx / B;
+    const FftGeom fg = fft_geom(L, B, 1, se, 0);
+    fft_lines<DIR>(s, fg, tw);
+    for (int idx = threadIdx.x; idx < (nout << lgB); idx += blockDim.x) {
+        int b = idx & (B - 1), r = idx >> lgB;
         int col = col0 + b;
         if (col < Hx) ob[r * g.rs_out + col] = s[r * se + b];
     }
@@ -175,55 +188,57 @@ __global__ void k_cols(const C_t<T>* in, C_t<T>* out, int L, int nin, int nout, 
 // Per (ky, tile of B kx): z-FFT of the three components (nz of Pz rows
 // non-zero), H^ = -N^ M^ with the symmetric 3x3 real tensor from the octant
 // (N_xy odd in ky, N_xz odd in kz, N_yz odd in both), z-inverse, keep nz.
+// Shared memory: three batches (components) of B lines of length Pz.
 template <typename T>
-__global__ void k_zconv(C_t<T>* buf, const T* __restrict__ kern, int nz, int Pz, int Py, int Hs, int Hx,
-                        int Py2, int Pz2, int B, const C_t<T>* __restrict__ twz) {
+__global__ void k_zconv(C_t<T>* buf, const T* __restrict__ kern, int nz, int lgPz, int Py, int Hs, int Hx,
+                        int Py2, int Pz2, int lgB, const C_t<T>* __restrict__ twz) {
     using C = C_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
-    const int nl = 3 * B, se = nl + 1;
-    const int col0 = blockIdx.x * B;
+    const int Pz = 1 << lgPz, B = 1 << lgB;
+    const int se = B + 1, bs = Pz * se;
+    const int col0 = blockIdx.x << lgB;
     const int ky = blockIdx.y;
     const long zstride = (long)Py * Hs;
     const long cstride = (long)nz * zstride;
     C* base = buf + (long)ky * Hs + col0;
-    for (int idx = threadIdx.x; idx < Pz * nl; idx += blockDim.x) {
-        int b = idx % B, rest = idx / B;
-        int c = rest % 3, z = rest / 3;
+    for (int idx = threadIdx.x; idx < 3 * (Pz << lgB); idx += blockDim.x) {
+        int b = idx & (B - 1), rest = idx >> lgB;   // rest = c * Pz + z
+        int c = rest >> lgPz, z = rest & (Pz - 1);
         C v = cmk<C>(0, 0);
         if (z < nz && col0 + b < Hx) v = base[c * cstride + z * zstride + b];
-        s[z * se + c * B + b] = v;
+        s[c * bs + z * se + b] = v;
     }
     __syncthreads();
-    fft_lines<-1>(s, Pz, nl, se, twz);
-    const int kyp = ky <= Py / 2 ? ky : Py - ky;
-    const T sy = ky > Py / 2 ? (T)-1 : (T)1;
+    const FftGeom fg = fft_geom(Pz, B, 3, se, bs);
+    fft_lines<-1>(s, fg, twz);
+    const int kyp = ky <= (Py >> 1) ? ky : Py - ky;
+    const T sy = ky > (Py >> 1) ? (T)-1 : (T)1;
     const long kstride = (long)Pz2 * Py2 * Hs;
-    for (int idx = threadIdx.x; idx < Pz * B; idx += blockDim.x) {
-        int b = idx % B, kz = idx / B;
+    for (int idx = threadIdx.x; idx < (Pz << lgB); idx += blockDim.x) {
+        int b = idx & (B - 1), kz = idx >> lgB;
         int col = col0 + b;
         if (col >= Hx) continue;
-        int kzp = kz <= Pz / 2 ? kz : Pz - kz;
-        T sz = kz > Pz / 2 ? (T)-1 : (T)1;
+        int kzp = kz <= (Pz >> 1) ? kz : Pz - kz;
+        T sz = kz > (Pz >> 1) ? (T)-1 : (T)1;
         long kb = ((long)kzp * Py2 + kyp) * Hs + col;
         T nxx = kern[kb], nyy = kern[kstride + kb], nzz = kern[2 * kstride + kb];
         T nxy = sy * kern[3 * kstride + kb];
         T nxz = sz * kern[4 * kstride + kb];
         T nyz = sy * sz * kern[5 * kstride + kb];
-        C mx = s[kz * se + b], my = s[kz * se + B + b], mz = s[kz * se + 2 * B + b];
-        C hx = cmk<C>(-(nxx * mx.x + nxy * my.x + nxz * mz.x), -(nxx * mx.y + nxy * my.y + nxz * mz.y));
-        C hy = cmk<C>(-(nxy * mx.x + nyy * my.x + nyz * mz.x), -(nxy * mx.y + nyy * my.y + nyz * mz.y));
-        C hz = cmk<C>(-(nxz * mx.x + nyz * my.x + nzz * mz.x), -(nxz * mx.y + nyz * my.y + nzz * mz.y));
-        s[kz * se + b] = hx;
-        s[kz * se + B + b] = hy;
-        s[kz * se + 2 * B + b] = hz;
+        const int o = kz * se + b;
+        C mx = s[o], my = s[bs + o], mz = s[2 * bs + o];
+        s[o] = cmk<C>(-(nxx * mx.x + nxy * my.x + nxz * mz.x), -(nxx * mx.y + nxy * my.y + nxz * mz.y));
+        s[bs + o] = cmk<C>(-(nxy * mx.x + nyy * my.x + nyz * mz.x), -(nxy * mx.y + nyy * my.y + nyz * mz.y));
+        s[2 * bs + o] = cmk<C>(-(nxz * mx.x + nyz * my.x + nzz * mz.x), -(nxz * mx.y + nyz * my.y + nzz * mz.y));
     }
     __syncthreads();
-    fft_lines<+1>(s, Pz, nl, se, twz);
-    for (int idx = threadIdx.x; idx < nz * nl; idx += blockDim.x) {
-        int b = idx % B, rest = idx / B;
-        int c = rest % 3, z = rest / 3;
-        if (col0 + b < Hx) base[c * cstride + z * zstride + b] = s[z * se + c * B + b];
+    fft_lines<+1>(s, fg, twz);
+    const int lgnz = lgPz > 0 ? lgPz - 1 : 0;       // nz = Pz / 2, or 1 when Pz = 1
+    for (int idx = threadIdx.x; idx < 3 * (nz << lgB); idx += blockDim.x) {
+        int b = idx & (B - 1), rest = idx >> lgB;   // rest = c * nz + z
+        int c = rest >> lgnz, z = rest & (nz - 1);
+        if (col0 + b < Hx) base[c * cstride + z * zstride + b] = s[c * bs + z * se + b];
     }
 }
 
@@ -249,22 +264,23 @@ inline int block_threads(int nact) {
     return t > 1024 ? 1024 : t;
 }
 
-inline int pow2_floor(int v) {
+inline int clamp_pow2(int v, int lo, int hi) {
     int p = 1;
     while (p * 2 <= v) p *= 2;
+    if (p < lo) p = lo;
+    if (p > hi) p = hi;
     return p;
 }
 
-// lines per block for a transform of length L of complex elements of size cs
-inline int lines_per_block(int L, int cs, int extra_factor) {
-    // active threads nlines*L/8 <= 1024, shared memory <= 64 KiB, at most 64
-    int by_threads = 8192 / (L * extra_factor);
-    int by_smem = 65536 / (L * cs * extra_factor);
-    int b = by_threads < by_smem ? by_threads : by_smem;
-    if (b > 64) b = 64;
-    if (b < 1) b = 1;
-    b = pow2_floor(b);
-    if (L * extra_factor < 8 && b < 8) b = 8;   // nlines*L must be a multiple of 8
+// rows per block of the x passes: about 256 active threads, at least 4 rows
+inline int x_rows_per_block(int L) { return clamp_pow2(2048 / L, 4, 64); }
+// columns per block of the y passes: at least 32 bytes of each row, at most
+// 512 active threads
+inline int col_tile(int L, int cs) { return clamp_pow2(4096 / L, 32 / cs, 32); }
+// columns per block of the z pass (three components each)
+inline int z_tile(int Pz, int cs) {
+    int b = clamp_pow2(Pz >= 8 ? 2048 / Pz : 32, 32 / cs, 32);
+    if (Pz < 8 && b * Pz < 8) b = 8 / Pz;
     return b;
 }
 
@@ -272,7 +288,6 @@ template <typename T> const C_t<T>* table(const mm_ctx* ctx, long off);
 template <> const double2* table<double>(const mm_ctx* ctx, long off) { return (const double2*)ctx->tw.f64 + off; }
 template <> const float2* table<float>(const mm_ctx* ctx, long off) { return (const float2*)ctx->tw.f32 + off; }
 
-template <typename T>
 int set_smem(mm_ctx* ctx, const void* fn, size_t bytes) {
     if (bytes > 48 * 1024) {
         MM_CUDA_CHECK(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
@@ -291,12 +306,12 @@ int run_xfwd(mm_ctx* ctx, const T* in, long in_ld, int nin, const T* Ms, T ms, l
         return MM_OK;
     }
     const int L = Px / 2;
-    const int B = lines_per_block(L, sizeof(C_t<T>), 1);
+    const int B = x_rows_per_block(L);
     size_t smem = (size_t)L * (B + 1) * sizeof(C_t<T>);
-    int rc = set_smem<T>(ctx, (const void*)k_xfwd<T>, smem);
+    int rc = set_smem(ctx, (const void*)k_xfwd<T>, smem);
     if (rc) return rc;
     k_xfwd<T><<<(unsigned)((rows + B - 1) / B), block_threads(B * L / 8), smem, ctx->stream>>>(
-        in, in_ld, nin, Ms, ms, ms_rows, out, ctx->Hs, L, rows, B, twL, twP);
+        in, in_ld, nin, Ms, ms, ms_rows, out, ctx->Hs, ilog2(L), rows, ilog2(B), twL, twP);
     MM_LAUNCH_CHECK(ctx);
     return MM_OK;
 }
@@ -305,12 +320,13 @@ template <typename T, int DIR>
 int run_cols(mm_ctx* ctx, const C_t<T>* in, C_t<T>* out, int L, int nin, int nout, int nplanes, ColGeom g,
              const C_t<T>* tw) {
     KernelTimer kt(ctx, DIR < 0 ? MM_K_YFWD : MM_K_YINV);
-    const int B = lines_per_block(L, sizeof(C_t<T>), 1);
+    const int B = col_tile(L, sizeof(C_t<T>));
     size_t smem = (size_t)L * (B + 1) * sizeof(C_t<T>);
-    int rc = set_smem<T>(ctx, (const void*)k_cols<T, DIR>, smem);
+    int rc = set_smem(ctx, (const void*)k_cols<T, DIR>, smem);
     if (rc) return rc;
     dim3 grid((unsigned)((ctx->Hx + B - 1) / B), (unsigned)nplanes);
-    k_cols<T, DIR><<<grid, block_threads(B * L / 8), smem, ctx->stream>>>(in, out, L, nin, nout, ctx->Hx, B, g, tw);
+    k_cols<T, DIR><<<grid, block_threads(B * L / 8), smem, ctx->stream>>>(in, out, ilog2(L), nin, nout, ctx->Hx,
+                                                                          ilog2(B), g, tw);
     MM_LAUNCH_CHECK(ctx);
     return MM_OK;
 }
@@ -340,14 +356,13 @@ int apply(mm_ctx* ctx, const T* m, T* H) {
     {
         KernelTimer kt(ctx, MM_K_ZCONV);
         const int Pz = ctx->Pz;
-        int B = Pz >= 8 ? lines_per_block(Pz, sizeof(C), 3) : 16;
-        if (B > 16) B = 16;
-        size_t smem = (size_t)Pz * (3 * B + 1) * sizeof(C);
-        rc = set_smem<T>(ctx, (const void*)k_zconv<T>, smem);
+        const int B = z_tile(Pz, sizeof(C));
+        size_t smem = (size_t)3 * Pz * (B + 1) * sizeof(C);
+        rc = set_smem(ctx, (const void*)k_zconv<T>, smem);
         if (rc) return rc;
         dim3 grid((unsigned)((ctx->Hx + B - 1) / B), (unsigned)ctx->Py);
         k_zconv<T><<<grid, block_threads(3 * B * Pz / 8), smem, ctx->stream>>>(
-            Bf, (const T*)ctx->kern, ctx->nz, Pz, ctx->Py, ctx->Hs, ctx->Hx, ctx->Py2, ctx->Pz2, B,
+            Bf, (const T*)ctx->kern, ctx->nz, ilog2(Pz), ctx->Py, ctx->Hs, ctx->Hx, ctx->Py2, ctx->Pz2, ilog2(B),
             table<T>(ctx, ctx->tw.off_pz));
         MM_LAUNCH_CHECK(ctx);
     }
@@ -366,12 +381,13 @@ int apply(mm_ctx* ctx, const T* m, T* H) {
         MM_LAUNCH_CHECK(ctx);
     } else {
         const int L = ctx->Lx;
-        const int B = lines_per_block(L, sizeof(C), 1);
+        const int B = x_rows_per_block(L);
         size_t smem = (size_t)L * (B + 1) * sizeof(C);
-        rc = set_smem<T>(ctx, (const void*)k_xinv<T>, smem);
+        rc = set_smem(ctx, (const void*)k_xinv<T>, smem);
         if (rc) return rc;
         k_xinv<T><<<(unsigned)((rows + B - 1) / B), block_threads(B * L / 8), smem, ctx->stream>>>(
-            xin, ctx->Hs, H, ctx->nx, L, rows, B, scale, table<T>(ctx, ctx->tw.off_lx), table<T>(ctx, ctx->tw.off_px));
+            xin, ctx->Hs, H, ctx->nx, ilog2(L), rows, ilog2(B), scale, table<T>(ctx, ctx->tw.off_lx),
+            table<T>(ctx, ctx->tw.off_px));
         MM_LAUNCH_CHECK(ctx);
     }
     return MM_OK;

@@ -1,23 +1,31 @@
 // Batched shared-memory FFT engine used by the demag passes.
 //
-// A thread block holds `nlines` complex lines of power-of-two length L in
-// shared memory, element e of line b at s[e * se + b] (se = nlines + 1, the
-// pad keeps strided accesses bank-conflict free).  The transform is the
-// Stockham autosort formulation: stage after stage of radix R (8 while the
-// remaining length allows, then 4 or 2), each taking the R elements
-// j + r L/R, twiddling by w^(k r) with k = j mod Ns, doing an R-point DFT in
-// registers and storing at (j / Ns) Ns R + k + r Ns, where Ns is the product
-// of the radices already applied.  Output is in natural order, unnormalised.
+// A thread block holds `nb` batches of `NL` complex lines of power-of-two
+// length L in shared memory: element e of line b of batch a at
+// s[a * bs + e * se + b] (se >= NL pads rows so strided accesses do not
+// collide in one bank).  The transform is the Stockham autosort
+// formulation: stage after stage of radix R (8 while the remaining length
+// allows, then 4 or 2), each taking the R elements j + r L/R, twiddling by
+// w^(k r) with k = j mod Ns, doing an R-point DFT in registers and storing at
+// (j / Ns) Ns R + k + r Ns, where Ns is the product of the radices already
+// applied.  Output is in natural order, unnormalised.
 //
-// Each active thread owns 8 elements per stage (8/R groups), so a block needs
-// nlines * L / 8 active threads; the stage reads all of them into registers,
-// synchronises, then writes, which makes the update in place.  Extra threads
-// only take part in the barriers.
+// Every size is a power of two, so all index arithmetic is shifts and masks.
+// Each active thread owns 8 elements per stage (8/R groups); a block needs
+// nb * NL * L / 8 active threads.  The stage reads all of them into
+// registers, synchronises, then writes, which makes the update in place.
+// Extra threads only take part in the barriers.
 #pragma once
 
 #include "mm_internal.cuh"
 
 namespace mm {
+
+__host__ __device__ __forceinline__ int ilog2(int v) {
+    int r = 0;
+    while ((1 << r) < v) ++r;
+    return r;
+}
 
 // multiply by DIR * i (DIR = -1 forward, +1 inverse)
 template <int DIR, typename C> __device__ __forceinline__ C mul_i(C a) {
@@ -47,9 +55,9 @@ template <int DIR, typename C> __device__ __forceinline__ void dft8(C* v) {
     dft4<DIR>(e0, e1, e2, e3);
     dft4<DIR>(o0, o1, o2, o3);
     // W8^k = exp(DIR 2 pi i k / 8)
-    C w1o = cmul(o1, cmk<C>(h, DIR * h));
+    C w1o = cmk<C>(h * (o1.x - DIR * o1.y), h * (o1.y + DIR * o1.x));
     C w2o = mul_i<DIR>(o2);
-    C w3o = cmul(o3, cmk<C>(-h, DIR * h));
+    C w3o = cmk<C>(-h * (o3.x + DIR * o3.y), h * (DIR * o3.x - o3.y));
     v[0] = cadd(e0, o0);
     v[4] = csub(e0, o0);
     v[1] = cadd(e1, w1o);
@@ -66,44 +74,74 @@ template <int R, int DIR, typename C> __device__ __forceinline__ void dftR(C* v)
     else dft2<DIR>(v);
 }
 
+// Geometry of the lines a block transforms (all counts powers of two except nb).
+struct FftGeom {
+    int L, lgL;     // line length
+    int NL, lgNL;   // lines per batch
+    int nb;         // batches
+    int se;         // shared-memory row stride (elements)
+    int bs;         // shared-memory batch stride (elements)
+    int nact;       // active threads: nb * NL * L / 8
+};
+
+__host__ __device__ inline FftGeom fft_geom(int L, int NL, int nb, int se, int bs) {
+    FftGeom g;
+    g.L = L;
+    g.lgL = ilog2(L);
+    g.NL = NL;
+    g.lgNL = ilog2(NL);
+    g.nb = nb;
+    g.se = se;
+    g.bs = bs;
+    g.nact = (nb * NL * L) >> 3;
+    return g;
+}
+
 // One radix-R Stockham stage on all lines of the block.
 // tw: exp(-2 pi i m / L), m < L.
 template <int R, int DIR, typename C>
-__device__ __forceinline__ void fft_stage(C* s, int L, int Ns, int nlines, int se, int nact,
-                                          const C* __restrict__ tw) {
+__device__ __forceinline__ void fft_stage(C* s, const FftGeom& g, int lgNs, const C* __restrict__ tw) {
     constexpr int G = 8 / R;
+    constexpr int lgR = R == 8 ? 3 : R == 4 ? 2 : 1;
     const int tid = threadIdx.x;
-    const int per_line = L / R;
+    const int lgPer = g.lgL - lgR;                 // log2(L / R)
+    const int lgBatch = g.lgNL + lgPer;            // groups per batch
+    const int Ns = 1 << lgNs;
     C v[G][R];
-    if (tid < nact) {
+    int base[G], kk[G], jj[G];
+    if (tid < g.nact) {
 #pragma unroll
         for (int q = 0; q < G; ++q) {
-            int g = q * nact + tid;
-            int line = g % nlines, j = g / nlines;
+            int gi = q * g.nact + tid;
+            int a = gi >> lgBatch;
+            int rem = gi & ((1 << lgBatch) - 1);
+            int line = rem & (g.NL - 1);
+            int j = rem >> g.lgNL;
+            base[q] = a * g.bs + line;
+            jj[q] = j;
+            kk[q] = j & (Ns - 1);
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[q][r] = s[(j + r * per_line) * se + line];
+            for (int r = 0; r < R; ++r) v[q][r] = s[base[q] + ((j + (r << lgPer)) * g.se)];
         }
     }
     __syncthreads();
-    if (tid < nact) {
-        const int step = L / (Ns * R);
+    if (tid < g.nact) {
+        const int lgStep = g.lgL - lgNs - lgR;     // log2(L / (Ns R))
 #pragma unroll
         for (int q = 0; q < G; ++q) {
-            int g = q * nact + tid;
-            int line = g % nlines, j = g / nlines;
-            int k = j % Ns;
-            if (Ns > 1) {
+            const int k = kk[q];
+            if (lgNs > 0) {
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    C w = tw[k * r * step];
+                    C w = tw[(k * r) << lgStep];
                     if (DIR > 0) w = cconj(w);
                     v[q][r] = cmul(v[q][r], w);
                 }
             }
             dftR<R, DIR>(v[q]);
-            int idxD = (j / Ns) * Ns * R + k;
+            const int idxD = ((jj[q] >> lgNs) << (lgNs + lgR)) + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) s[(idxD + r * Ns) * se + line] = v[q][r];
+            for (int r = 0; r < R; ++r) s[base[q] + (idxD + (r << lgNs)) * g.se] = v[q][r];
         }
     }
     __syncthreads();
@@ -111,16 +149,15 @@ __device__ __forceinline__ void fft_stage(C* s, int L, int Ns, int nlines, int s
 
 // Full transform of every line.  Must be called by all threads of the block.
 template <int DIR, typename C>
-__device__ void fft_lines(C* s, int L, int nlines, int se, const C* __restrict__ tw) {
-    const int nact = (nlines * L) / 8;
-    int Ns = 1, rem = L;
-    while (rem >= 8) {
-        fft_stage<8, DIR>(s, L, Ns, nlines, se, nact, tw);
-        Ns *= 8;
-        rem /= 8;
+__device__ void fft_lines(C* s, const FftGeom& g, const C* __restrict__ tw) {
+    int lgNs = 0, rem = g.lgL;
+    while (rem >= 3) {
+        fft_stage<8, DIR>(s, g, lgNs, tw);
+        lgNs += 3;
+        rem -= 3;
     }
-    if (rem == 4) fft_stage<4, DIR>(s, L, Ns, nlines, se, nact, tw);
-    else if (rem == 2) fft_stage<2, DIR>(s, L, Ns, nlines, se, nact, tw);
+    if (rem == 2) fft_stage<4, DIR>(s, g, lgNs, tw);
+    else if (rem == 1) fft_stage<2, DIR>(s, g, lgNs, tw);
 }
 
 }  // namespace mm
