@@ -34,52 +34,57 @@ template <typename T> using C_t = typename cx<T>::type;
 //   B = 2^lgB rows per block, row r at in + r*in_ld, nin real values (even
 //   count, rest zero); Ms: per-cell array indexed (r mod ms_rows)*in_ld + x,
 //   or nullptr (scalar ms).  Complex length L = 2^lgL = Px / 2.
+//   Shared memory: B lines of L (FftGeom layout); global accesses run with
+//   the row index b fastest across a warp (B row segments per instruction).
 template <typename T>
-__global__ void k_xfwd(const T* __restrict__ in, long in_ld, int nin, const T* __restrict__ Ms, T ms,
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_xfwd(const T* __restrict__ in, long in_ld, int nin, const T* __restrict__ Ms, T ms,
                        long ms_rows, C_t<T>* __restrict__ out, int Hs, int lgL, long rows, int lgB,
                        const C_t<T>* __restrict__ twL, const C_t<T>* __restrict__ twP) {
     using C = C_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
     const int L = 1 << lgL, B = 1 << lgB;
-    const int se = B + 1;
+    const FftGeom g = fft_geom(L, B, 1, sizeof(C));
     const long r0 = (long)blockIdx.x << lgB;
     const int npair = nin >> 1;
-    for (int idx = threadIdx.x; idx < (B << lgL); idx += blockDim.x) {
-        int b = idx >> lgL, j = idx & (L - 1);
-        long r = r0 + b;
-        C v = cmk<C>(0, 0);
-        if (j < npair && r < rows) {
-            v = reinterpret_cast<const C*>(in + r * in_ld)[j];
-            if (Ms) {
-                C w = reinterpret_cast<const C*>(Ms + (r % ms_rows) * in_ld)[j];
-                v.x *= w.x;
-                v.y *= w.y;
-            } else {
-                v.x *= ms;
-                v.y *= ms;
+    constexpr int U = 4;
+    const int total = B << lgL;
+    for (int base = threadIdx.x; base < total; base += U * blockDim.x) {
+        C v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            int idx = base + u * blockDim.x;
+            int b = idx & (B - 1), j = idx >> lgB;
+            long r = r0 + b;
+            v[u] = cmk<C>(0, 0);
+            if (idx < total && j < npair && r < rows) {
+                v[u] = reinterpret_cast<const C*>(in + r * in_ld)[j];
+                if (Ms) {
+                    C w = reinterpret_cast<const C*>(Ms + (r % ms_rows) * in_ld)[j];
+                    v[u].x *= w.x;
+                    v[u].y *= w.y;
+                } else {
+                    v[u].x *= ms;
+                    v[u].y *= ms;
+                }
             }
         }
-        s[j * se + b] = v;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            int idx = base + u * blockDim.x;
+            if (idx < total) s[sidx(g, 0, idx >> lgB, idx & (B - 1))] = v[u];
+        }
     }
     __syncthreads();
-    const FftGeom g = fft_geom(L, B, 1, se, 0);
     fft_lines<-1>(s, g, twL);
     const T half = (T)0.5;
     // X_k = E_k - i w^k D_k, E, D the even/odd split of the packed spectrum Z
-    for (int idx = threadIdx.x; idx < (B << lgL) + B; idx += blockDim.x) {
-        int b, k;
-        if (idx < (B << lgL)) {
-            b = idx >> lgL;
-            k = idx & (L - 1);
-        } else {
-            b = idx - (B << lgL);
-            k = L;
-        }
+    for (int idx = threadIdx.x; idx < total + B; idx += blockDim.x) {
+        int b = idx & (B - 1), k = idx >> lgB;        // k runs 0..L
         long r = r0 + b;
         if (r >= rows) continue;
-        C zk = s[(k & (L - 1)) * se + b];
-        C zc = cconj(s[((L - k) & (L - 1)) * se + b]);
+        C zk = s[sidx(g, 0, k & (L - 1), b)];
+        C zc = cconj(s[sidx(g, 0, (L - k) & (L - 1), b)]);
         C e = cscale(cadd(zk, zc), half);
         C d = cscale(csub(zk, zc), half);
         C wd = cmul(twP[k], d);
@@ -100,38 +105,49 @@ __global__ void k_x1fwd(const T* __restrict__ in, const T* __restrict__ Ms, T ms
 // ------------------------------------------------------------------ K6
 // Hx frequencies -> inverse packed complex FFT -> nx real outputs, scaled.
 template <typename T>
-__global__ void k_xinv(const C_t<T>* __restrict__ in, int Hs, T* __restrict__ out, int nx, int lgL, long rows,
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_xinv(const C_t<T>* __restrict__ in, int Hs, T* __restrict__ out, int nx, int lgL, long rows,
                        int lgB, T scale, const C_t<T>* __restrict__ twL, const C_t<T>* __restrict__ twP) {
     using C = C_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
     const int L = 1 << lgL, B = 1 << lgB;
-    const int se = B + 1;
+    const FftGeom g = fft_geom(L, B, 1, sizeof(C));
     const long r0 = (long)blockIdx.x << lgB;
     const T half = (T)0.5;
-    for (int idx = threadIdx.x; idx < (B << lgL); idx += blockDim.x) {
-        int b = idx >> lgL, k = idx & (L - 1);
-        long r = r0 + b;
-        C z = cmk<C>(0, 0);
-        if (r < rows) {
-            C xk = in[r * Hs + k];
-            C xc = cconj(in[r * Hs + (L - k)]);
-            C e = cscale(cadd(xk, xc), half);
-            C o = cmul(cscale(csub(xk, xc), half), cconj(twP[k]));   // times exp(+2 pi i k / Px)
-            z = cmk<C>(e.x - o.y, e.y + o.x);                          // E + i O
+    constexpr int U = 2;
+    const int total = B << lgL;
+    for (int base = threadIdx.x; base < total; base += U * blockDim.x) {
+        C xk[U], xc[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            int idx = base + u * blockDim.x;
+            int b = idx & (B - 1), k = idx >> lgB;
+            long r = r0 + b;
+            xk[u] = cmk<C>(0, 0);
+            xc[u] = cmk<C>(0, 0);
+            if (idx < total && r < rows) {
+                xk[u] = in[r * Hs + k];
+                xc[u] = cconj(in[r * Hs + (L - k)]);
+            }
         }
-        s[k * se + b] = z;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            int idx = base + u * blockDim.x;
+            if (idx >= total) continue;
+            int b = idx & (B - 1), k = idx >> lgB;
+            C e = cscale(cadd(xk[u], xc[u]), half);
+            C o = cmul(cscale(csub(xk[u], xc[u]), half), cconj(twP[k]));   // times exp(+2 pi i k / Px)
+            s[sidx(g, 0, k, b)] = cmk<C>(e.x - o.y, e.y + o.x);            // E + i O
+        }
     }
     __syncthreads();
-    const FftGeom g = fft_geom(L, B, 1, se, 0);
     fft_lines<+1>(s, g, twL);
     const int lgP = ilog2(nx >> 1);
-    const int npair = nx >> 1;
     for (int idx = threadIdx.x; idx < (B << lgP); idx += blockDim.x) {
-        int b = idx >> lgP, j = idx & (npair - 1);
+        int b = idx & (B - 1), j = idx >> lgB;
         long r = r0 + b;
         if (r >= rows) continue;
-        C z = s[j * se + b];
+        C z = s[sidx(g, 0, j, b)];
         reinterpret_cast<C*>(out + r * (long)nx)[j] = cmk<C>(z.x * scale, z.y * scale);
     }
 }
@@ -155,91 +171,129 @@ struct ColGeom {
 };
 
 template <typename T, int DIR>
-__global__ void k_cols(const C_t<T>* in, C_t<T>* out, int lgL, int nin, int nout, int Hx, int lgB, ColGeom g,
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_cols(const C_t<T>* in, C_t<T>* out, int lgL, int nin, int nout, int Hx, int lgB, ColGeom cg,
                        const C_t<T>* __restrict__ tw) {
     using C = C_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
     const int L = 1 << lgL, B = 1 << lgB;
-    const int se = B + 1;
+    const FftGeom g = fft_geom(L, B, 1, sizeof(C));
     const int col0 = blockIdx.x << lgB;
     const int p = blockIdx.y;
-    const int pi = p % g.n_inner, po = p / g.n_inner;
-    const C* ib = in + pi * g.in_inner + po * g.in_outer;
-    C* ob = out + pi * g.out_inner + po * g.out_outer;
-    for (int idx = threadIdx.x; idx < (L << lgB); idx += blockDim.x) {
-        int b = idx & (B - 1), r = idx >> lgB;
-        int col = col0 + b;
-        C v = cmk<C>(0, 0);
-        if (r < nin && col < Hx) v = ib[r * g.rs_in + col];
-        s[r * se + b] = v;
+    const int pi = p % cg.n_inner, po = p / cg.n_inner;
+    const C* ib = in + pi * cg.in_inner + po * cg.in_outer;
+    C* ob = out + pi * cg.out_inner + po * cg.out_outer;
+    constexpr int U = 4;
+    const int total = L << lgB;
+    for (int base = threadIdx.x; base < total; base += U * blockDim.x) {
+        C v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            int idx = base + u * blockDim.x;
+            int b = idx & (B - 1), r = idx >> lgB;
+            v[u] = cmk<C>(0, 0);
+            if (idx < total && r < nin && col0 + b < Hx) v[u] = ib[r * cg.rs_in + col0 + b];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            int idx = base + u * blockDim.x;
+            if (idx < total) s[sidx(g, 0, idx >> lgB, idx & (B - 1))] = v[u];
+        }
     }
     __syncthreads();
-    const FftGeom fg = fft_geom(L, B, 1, se, 0);
-    fft_lines<DIR>(s, fg, tw);
+    fft_lines<DIR>(s, g, tw);
     for (int idx = threadIdx.x; idx < (nout << lgB); idx += blockDim.x) {
         int b = idx & (B - 1), r = idx >> lgB;
-        int col = col0 + b;
-        if (col < Hx) ob[r * g.rs_out + col] = s[r * se + b];
+        if (col0 + b < Hx) ob[r * cg.rs_out + col0 + b] = s[sidx(g, 0, r, b)];
     }
 }
 
 // ------------------------------------------------------------------ K4
-// Per (ky, tile of B kx): z-FFT of the three components (nz of Pz rows
-// non-zero), H^ = -N^ M^ with the symmetric 3x3 real tensor from the octant
-// (N_xy odd in ky, N_xz odd in kz, N_yz odd in both), z-inverse, keep nz.
-// Shared memory: three batches (components) of B lines of length Pz.
+// Per (ky pair, tile of B kx): for ky and Py - ky, z-FFT of the three
+// components (nz of Pz rows non-zero), H^ = -N^ M^ with the symmetric 3x3
+// real tensor from the octant (N_xy odd in ky, N_xz odd in kz, N_yz odd in
+// both), z-inverse, keep nz rows.  The octant rows of the tile are read once
+// into shared memory and serve both ky.  Shared memory: three batches
+// (components) of B lines of length Pz, then the 6 x (Pz/2+1) x B octant.
 template <typename T>
-__global__ void k_zconv(C_t<T>* buf, const T* __restrict__ kern, int nz, int lgPz, int Py, int Hs, int Hx,
-                        int Py2, int Pz2, int lgB, const C_t<T>* __restrict__ twz) {
+__device__ __forceinline__ void zconv_one(C_t<T>* s, const T* kn, const FftGeom& g, C_t<T>* base, T sy, int nz,
+                                          int lgPz, int Pz2, int lgB, int Hx, int col0, long zstride, long cstride,
+                                          const C_t<T>* __restrict__ twz) {
+    using C = C_t<T>;
+    const int Pz = 1 << lgPz, B = 1 << lgB;
+    __syncthreads();
+    constexpr int U = 4;
+    const int total = 3 * (Pz << lgB);
+    for (int b0 = threadIdx.x; b0 < total; b0 += U * blockDim.x) {
+        C v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            int idx = b0 + u * blockDim.x;
+            int b = idx & (B - 1), rest = idx >> lgB;   // rest = c * Pz + z
+            int c = rest >> lgPz, z = rest & (Pz - 1);
+            v[u] = cmk<C>(0, 0);
+            if (idx < total && z < nz && col0 + b < Hx) v[u] = base[c * cstride + z * zstride + b];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            int idx = b0 + u * blockDim.x;
+            if (idx >= total) continue;
+            int b = idx & (B - 1), rest = idx >> lgB;
+            s[sidx(g, rest >> lgPz, rest & (Pz - 1), b)] = v[u];
+        }
+    }
+    __syncthreads();
+    fft_lines<-1>(s, g, twz);
+    const int ks = Pz2 << lgB;
+    for (int idx = threadIdx.x; idx < (Pz << lgB); idx += blockDim.x) {
+        int b = idx & (B - 1), kz = idx >> lgB;
+        int kzp = kz <= (Pz >> 1) ? kz : Pz - kz;
+        T sz = kz > (Pz >> 1) ? (T)-1 : (T)1;
+        const T* kk = kn + (kzp << lgB) + b;
+        T nxx = kk[0], nyy = kk[ks], nzz = kk[2 * ks];
+        T nxy = sy * kk[3 * ks];
+        T nxz = sz * kk[4 * ks];
+        T nyz = sy * sz * kk[5 * ks];
+        const int o0 = sidx(g, 0, kz, b), o1 = sidx(g, 1, kz, b), o2 = sidx(g, 2, kz, b);
+        C mx = s[o0], my = s[o1], mz = s[o2];
+        s[o0] = cmk<C>(-(nxx * mx.x + nxy * my.x + nxz * mz.x), -(nxx * mx.y + nxy * my.y + nxz * mz.y));
+        s[o1] = cmk<C>(-(nxy * mx.x + nyy * my.x + nyz * mz.x), -(nxy * mx.y + nyy * my.y + nyz * mz.y));
+        s[o2] = cmk<C>(-(nxz * mx.x + nyz * my.x + nzz * mz.x), -(nxz * mx.y + nyz * my.y + nzz * mz.y));
+    }
+    __syncthreads();
+    fft_lines<+1>(s, g, twz);
+    const int lgnz = lgPz > 0 ? lgPz - 1 : 0;               // nz = Pz / 2, or 1 when Pz = 1
+    for (int idx = threadIdx.x; idx < 3 * (nz << lgB); idx += blockDim.x) {
+        int b = idx & (B - 1), rest = idx >> lgB;       // rest = c * nz + z
+        int c = rest >> lgnz, z = rest & (nz - 1);
+        if (col0 + b < Hx) base[c * cstride + z * zstride + b] = s[sidx(g, c, z, b)];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512)
+    k_zconv(C_t<T>* buf, const T* __restrict__ kern, int nz, int lgPz, int Py, int Hs, int Hx, int Py2, int Pz2,
+            int lgB, const C_t<T>* __restrict__ twz) {
     using C = C_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
     const int Pz = 1 << lgPz, B = 1 << lgB;
-    const int se = B + 1, bs = Pz * se;
+    const FftGeom g = fft_geom(Pz, B, 3, sizeof(C));
+    T* kn = reinterpret_cast<T*>(s + 3 * (Pz << lgB));     // [6][Pz2][B]
     const int col0 = blockIdx.x << lgB;
-    const int ky = blockIdx.y;
+    const int kyp = blockIdx.y;                             // 0 .. Py/2
     const long zstride = (long)Py * Hs;
     const long cstride = (long)nz * zstride;
-    C* base = buf + (long)ky * Hs + col0;
-    for (int idx = threadIdx.x; idx < 3 * (Pz << lgB); idx += blockDim.x) {
-        int b = idx & (B - 1), rest = idx >> lgB;   // rest = c * Pz + z
-        int c = rest >> lgPz, z = rest & (Pz - 1);
-        C v = cmk<C>(0, 0);
-        if (z < nz && col0 + b < Hx) v = base[c * cstride + z * zstride + b];
-        s[c * bs + z * se + b] = v;
-    }
-    __syncthreads();
-    const FftGeom fg = fft_geom(Pz, B, 3, se, bs);
-    fft_lines<-1>(s, fg, twz);
-    const int kyp = ky <= (Py >> 1) ? ky : Py - ky;
-    const T sy = ky > (Py >> 1) ? (T)-1 : (T)1;
     const long kstride = (long)Pz2 * Py2 * Hs;
-    for (int idx = threadIdx.x; idx < (Pz << lgB); idx += blockDim.x) {
-        int b = idx & (B - 1), kz = idx >> lgB;
-        int col = col0 + b;
-        if (col >= Hx) continue;
-        int kzp = kz <= (Pz >> 1) ? kz : Pz - kz;
-        T sz = kz > (Pz >> 1) ? (T)-1 : (T)1;
-        long kb = ((long)kzp * Py2 + kyp) * Hs + col;
-        T nxx = kern[kb], nyy = kern[kstride + kb], nzz = kern[2 * kstride + kb];
-        T nxy = sy * kern[3 * kstride + kb];
-        T nxz = sz * kern[4 * kstride + kb];
-        T nyz = sy * sz * kern[5 * kstride + kb];
-        const int o = kz * se + b;
-        C mx = s[o], my = s[bs + o], mz = s[2 * bs + o];
-        s[o] = cmk<C>(-(nxx * mx.x + nxy * my.x + nxz * mz.x), -(nxx * mx.y + nxy * my.y + nxz * mz.y));
-        s[bs + o] = cmk<C>(-(nxy * mx.x + nyy * my.x + nyz * mz.x), -(nxy * mx.y + nyy * my.y + nyz * mz.y));
-        s[2 * bs + o] = cmk<C>(-(nxz * mx.x + nyz * my.x + nzz * mz.x), -(nxz * mx.y + nyz * my.y + nzz * mz.y));
+    for (int idx = threadIdx.x; idx < 6 * (Pz2 << lgB); idx += blockDim.x) {
+        int b = idx & (B - 1), rest = idx >> lgB;           // rest = c * Pz2 + kz
+        int c = rest / Pz2, kz = rest - c * Pz2;
+        kn[idx] = col0 + b < Hx ? kern[c * kstride + ((long)kz * Py2 + kyp) * Hs + col0 + b] : (T)0;
     }
-    __syncthreads();
-    fft_lines<+1>(s, fg, twz);
-    const int lgnz = lgPz > 0 ? lgPz - 1 : 0;       // nz = Pz / 2, or 1 when Pz = 1
-    for (int idx = threadIdx.x; idx < 3 * (nz << lgB); idx += blockDim.x) {
-        int b = idx & (B - 1), rest = idx >> lgB;   // rest = c * nz + z
-        int c = rest >> lgnz, z = rest & (nz - 1);
-        if (col0 + b < Hx) base[c * cstride + z * zstride + b] = s[c * bs + z * se + b];
-    }
+    zconv_one<T>(s, kn, g, buf + (long)kyp * Hs + col0, (T)1, nz, lgPz, Pz2, lgB, Hx, col0, zstride, cstride, twz);
+    if (kyp != 0 && 2 * kyp != Py)
+        zconv_one<T>(s, kn, g, buf + (long)(Py - kyp) * Hs + col0, (T)-1, nz, lgPz, Pz2, lgB, Hx, col0, zstride,
+                     cstride, twz);
 }
 
 // K1 tail: keep the real octant of the transformed component, at precision T.
@@ -277,9 +331,16 @@ inline int x_rows_per_block(int L) { return clamp_pow2(2048 / L, 4, 64); }
 // columns per block of the y passes: at least 32 bytes of each row, at most
 // 512 active threads
 inline int col_tile(int L, int cs) { return clamp_pow2(4096 / L, 32 / cs, 32); }
-// columns per block of the z pass (three components each)
+// columns per block of the z pass (three components each): at most 1024
+// (FP32) or 512 (FP64) active threads, at least 32 bytes of each row where
+// that limit allows
 inline int z_tile(int Pz, int cs) {
-    int b = clamp_pow2(Pz >= 8 ? 2048 / Pz : 32, 32 / cs, 32);
+    int cap = (cs == 8 ? 8192 : 4096) / (3 * Pz);       // nact = 3 B Pz / 8 <= 1024 or 512
+    int lo = 32 / cs;
+    int b = Pz >= 8 ? 1024 / Pz : 32;
+    if (b > cap) b = cap;
+    if (b < lo && lo <= cap) b = lo;
+    b = clamp_pow2(b, 1, 32);
     if (Pz < 8 && b * Pz < 8) b = 8 / Pz;
     return b;
 }
@@ -307,7 +368,7 @@ int run_xfwd(mm_ctx* ctx, const T* in, long in_ld, int nin, const T* Ms, T ms, l
     }
     const int L = Px / 2;
     const int B = x_rows_per_block(L);
-    size_t smem = (size_t)L * (B + 1) * sizeof(C_t<T>);
+    size_t smem = (size_t)L * B * sizeof(C_t<T>);
     int rc = set_smem(ctx, (const void*)k_xfwd<T>, smem);
     if (rc) return rc;
     k_xfwd<T><<<(unsigned)((rows + B - 1) / B), block_threads(B * L / 8), smem, ctx->stream>>>(
@@ -321,7 +382,7 @@ int run_cols(mm_ctx* ctx, const C_t<T>* in, C_t<T>* out, int L, int nin, int nou
              const C_t<T>* tw) {
     KernelTimer kt(ctx, DIR < 0 ? MM_K_YFWD : MM_K_YINV);
     const int B = col_tile(L, sizeof(C_t<T>));
-    size_t smem = (size_t)L * (B + 1) * sizeof(C_t<T>);
+    size_t smem = (size_t)L * B * sizeof(C_t<T>);
     int rc = set_smem(ctx, (const void*)k_cols<T, DIR>, smem);
     if (rc) return rc;
     dim3 grid((unsigned)((ctx->Hx + B - 1) / B), (unsigned)nplanes);
@@ -357,10 +418,10 @@ int apply(mm_ctx* ctx, const T* m, T* H) {
         KernelTimer kt(ctx, MM_K_ZCONV);
         const int Pz = ctx->Pz;
         const int B = z_tile(Pz, sizeof(C));
-        size_t smem = (size_t)3 * Pz * (B + 1) * sizeof(C);
+        size_t smem = (size_t)3 * Pz * B * sizeof(C) + (size_t)6 * ctx->Pz2 * B * sizeof(T);
         rc = set_smem(ctx, (const void*)k_zconv<T>, smem);
         if (rc) return rc;
-        dim3 grid((unsigned)((ctx->Hx + B - 1) / B), (unsigned)ctx->Py);
+        dim3 grid((unsigned)((ctx->Hx + B - 1) / B), (unsigned)(ctx->Py / 2 + 1));
         k_zconv<T><<<grid, block_threads(3 * B * Pz / 8), smem, ctx->stream>>>(
             Bf, (const T*)ctx->kern, ctx->nz, ilog2(Pz), ctx->Py, ctx->Hs, ctx->Hx, ctx->Py2, ctx->Pz2, ilog2(B),
             table<T>(ctx, ctx->tw.off_pz));
@@ -382,7 +443,7 @@ int apply(mm_ctx* ctx, const T* m, T* H) {
     } else {
         const int L = ctx->Lx;
         const int B = x_rows_per_block(L);
-        size_t smem = (size_t)L * (B + 1) * sizeof(C);
+        size_t smem = (size_t)L * B * sizeof(C);
         rc = set_smem(ctx, (const void*)k_xinv<T>, smem);
         if (rc) return rc;
         k_xinv<T><<<(unsigned)((rows + B - 1) / B), block_threads(B * L / 8), smem, ctx->stream>>>(

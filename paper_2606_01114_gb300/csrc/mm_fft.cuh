@@ -1,9 +1,7 @@
 // Batched shared-memory FFT engine used by the demag passes.
 //
 // A thread block holds `nb` batches of `NL` complex lines of power-of-two
-// length L in shared memory: element e of line b of batch a at
-// s[a * bs + e * se + b] (se >= NL pads rows so strided accesses do not
-// collide in one bank).  The transform is the Stockham autosort
+// length L in shared memory (layout and bank swizzle: FftGeom).  The transform is the Stockham autosort
 // formulation: stage after stage of radix R (8 while the remaining length
 // allows, then 4 or 2), each taking the R elements j + r L/R, twiddling by
 // w^(k r) with k = j mod Ns, doing an R-point DFT in registers and storing at
@@ -75,26 +73,66 @@ template <int R, int DIR, typename C> __device__ __forceinline__ void dftR(C* v)
 }
 
 // Geometry of the lines a block transforms (all counts powers of two except nb).
+// Element e of line `line` of batch a sits at a * L * NL + swz(e) * NL + line,
+// swz(e) = e ^ ((e >> 3) & sm): the XOR of the row index with bits above the
+// radix-8 group spreads the rows that one warp touches in a stage (8 apart in
+// the first stage) over all shared-memory banks; sm = 128 B / element size /
+// NL - 1 when a 128-byte bank row holds several rows, else 0.
 struct FftGeom {
     int L, lgL;     // line length
     int NL, lgNL;   // lines per batch
     int nb;         // batches
-    int se;         // shared-memory row stride (elements)
-    int bs;         // shared-memory batch stride (elements)
+    int sm;         // row swizzle mask
     int nact;       // active threads: nb * NL * L / 8
 };
 
-__host__ __device__ inline FftGeom fft_geom(int L, int NL, int nb, int se, int bs) {
+__host__ __device__ inline FftGeom fft_geom(int L, int NL, int nb, int elem_bytes) {
     FftGeom g;
     g.L = L;
     g.lgL = ilog2(L);
     g.NL = NL;
     g.lgNL = ilog2(NL);
     g.nb = nb;
-    g.se = se;
-    g.bs = bs;
+    int slots = 128 / elem_bytes;
+    g.sm = NL < slots ? slots / NL - 1 : 0;
     g.nact = (nb * NL * L) >> 3;
     return g;
+}
+
+__device__ __forceinline__ int sidx(const FftGeom& g, int a, int e, int line) {
+    return ((a << g.lgL) + (e ^ ((e >> 3) & g.sm))) * g.NL + line;
+}
+
+// twiddles w^r, r = 1..R-1, from w = tw[idx]: FP32 builds the powers by at
+// most three products of the tabulated value; FP64 reads each from the table.
+template <int R, int DIR, typename C>
+__device__ __forceinline__ void twiddle(C* v, const C* __restrict__ tw, int k, int lgStep) {
+    using T = decltype(C{}.x);
+    if constexpr (sizeof(T) == 4) {
+        C w1 = tw[k << lgStep];
+        if (DIR > 0) w1 = cconj(w1);
+        v[1] = cmul(v[1], w1);
+        if constexpr (R >= 4) {
+            C w2 = cmul(w1, w1);
+            C w3 = cmul(w2, w1);
+            v[2] = cmul(v[2], w2);
+            v[3] = cmul(v[3], w3);
+            if constexpr (R == 8) {
+                C w4 = cmul(w2, w2);
+                v[4] = cmul(v[4], w4);
+                v[5] = cmul(v[5], cmul(w4, w1));
+                v[6] = cmul(v[6], cmul(w3, w3));
+                v[7] = cmul(v[7], cmul(w4, w3));
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            C w = tw[(k * r) << lgStep];
+            if (DIR > 0) w = cconj(w);
+            v[r] = cmul(v[r], w);
+        }
+    }
 }
 
 // One radix-R Stockham stage on all lines of the block.
@@ -108,20 +146,18 @@ __device__ __forceinline__ void fft_stage(C* s, const FftGeom& g, int lgNs, cons
     const int lgBatch = g.lgNL + lgPer;            // groups per batch
     const int Ns = 1 << lgNs;
     C v[G][R];
-    int base[G], kk[G], jj[G];
+    int aa[G], ll[G], jj[G];
     if (tid < g.nact) {
 #pragma unroll
         for (int q = 0; q < G; ++q) {
             int gi = q * g.nact + tid;
             int a = gi >> lgBatch;
             int rem = gi & ((1 << lgBatch) - 1);
-            int line = rem & (g.NL - 1);
-            int j = rem >> g.lgNL;
-            base[q] = a * g.bs + line;
-            jj[q] = j;
-            kk[q] = j & (Ns - 1);
+            aa[q] = a;
+            ll[q] = rem & (g.NL - 1);
+            jj[q] = rem >> g.lgNL;
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[q][r] = s[base[q] + ((j + (r << lgPer)) * g.se)];
+            for (int r = 0; r < R; ++r) v[q][r] = s[sidx(g, a, jj[q] + (r << lgPer), ll[q])];
         }
     }
     __syncthreads();
@@ -129,19 +165,12 @@ __device__ __forceinline__ void fft_stage(C* s, const FftGeom& g, int lgNs, cons
         const int lgStep = g.lgL - lgNs - lgR;     // log2(L / (Ns R))
 #pragma unroll
         for (int q = 0; q < G; ++q) {
-            const int k = kk[q];
-            if (lgNs > 0) {
-#pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    C w = tw[(k * r) << lgStep];
-                    if (DIR > 0) w = cconj(w);
-                    v[q][r] = cmul(v[q][r], w);
-                }
-            }
+            const int k = jj[q] & (Ns - 1);
+            if (lgNs > 0) twiddle<R, DIR>(v[q], tw, k, lgStep);
             dftR<R, DIR>(v[q]);
             const int idxD = ((jj[q] >> lgNs) << (lgNs + lgR)) + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) s[base[q] + (idxD + (r << lgNs)) * g.se] = v[q][r];
+            for (int r = 0; r < R; ++r) s[sidx(g, aa[q], idxD + (r << lgNs), ll[q])] = v[q][r];
         }
     }
     __syncthreads();
