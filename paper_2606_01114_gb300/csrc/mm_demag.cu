@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "mm_fft.cuh"
+#include "mm_regfft.cuh"
 
 namespace mm {
 namespace {
@@ -296,6 +297,114 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512)
                      cstride, twz);
 }
 
+// ------------------------------------------- FP32 register-resident passes
+// K4 for Pz <= 32: one thread per (component, column) holds its whole z line
+// in registers; forward DFT (upper half zero), the 3x3 product through shared
+// memory (each thread forms its own component from all three), inverse DFT,
+// keep the nz un-padded rows.  Block: 3 x B threads, B = 2^lgB columns.
+template <int PZ>
+__global__ void __launch_bounds__(256)
+    k_zconv_reg(float2* buf, const float* __restrict__ kern, int Py, int Hs, int Hx, int Py2, int lgB) {
+    constexpr int NZ = PZ > 1 ? PZ / 2 : 1;
+    constexpr int PZ2 = PZ / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* S = reinterpret_cast<float2*>(smem_raw);      // [3][PZ][B]
+    const int B = 1 << lgB;
+    const int c = threadIdx.x >> lgB, b = threadIdx.x & (B - 1);
+    const int col = (blockIdx.x << lgB) + b;
+    const int ky = blockIdx.y;
+    const bool act = col < Hx;
+    const long zstride = (long)Py * Hs;
+    float2* p = buf + c * (NZ * zstride) + (long)ky * Hs + col;
+    float2 v[PZ];
+#pragma unroll
+    for (int z = 0; z < NZ; ++z) v[z] = act ? p[z * zstride] : make_float2(0.f, 0.f);
+    dif<PZ, -1, (PZ > 1)>(v);
+#pragma unroll
+    for (int kz = 0; kz < PZ; ++kz) S[(c * PZ + kz) * B + b] = v[dif_pos<PZ>(kz)];
+    __syncthreads();
+    const int kyp = ky <= (Py >> 1) ? ky : Py - ky;
+    const float sy = ky > (Py >> 1) ? -1.f : 1.f;
+    const long kstride = (long)PZ2 * Py2 * Hs;
+    // row c of the symmetric tensor: components (xx, xy, xz), (xy, yy, yz), (xz, yz, zz)
+    const int i0 = c == 0 ? 0 : c == 1 ? 3 : 4;
+    const int i1 = c == 0 ? 3 : c == 1 ? 1 : 5;
+    const int i2 = c == 0 ? 4 : c == 1 ? 5 : 2;
+    const float* kc = kern + ((long)kyp * Hs + (act ? col : 0));
+#pragma unroll
+    for (int kz = 0; kz < PZ; ++kz) {
+        const int kzp = kz <= PZ / 2 ? kz : PZ - kz;
+        const float sz = kz > PZ / 2 ? -1.f : 1.f;
+        // parity signs: xy odd in ky, xz odd in kz, yz odd in both
+        const float s0 = c == 0 ? 1.f : c == 1 ? sy : sz;
+        const float s1 = c == 0 ? sy : c == 1 ? 1.f : sy * sz;
+        const float s2 = c == 0 ? sz : c == 1 ? sy * sz : 1.f;
+        const long ko = (long)kzp * Py2 * Hs;
+        const float n0 = s0 * __ldg(kc + i0 * kstride + ko);
+        const float n1 = s1 * __ldg(kc + i1 * kstride + ko);
+        const float n2 = s2 * __ldg(kc + i2 * kstride + ko);
+        const float2 mx = S[kz * B + b], my = S[(PZ + kz) * B + b], mz = S[(2 * PZ + kz) * B + b];
+        v[kz] = make_float2(-(n0 * mx.x + n1 * my.x + n2 * mz.x), -(n0 * mx.y + n1 * my.y + n2 * mz.y));
+    }
+    dif<PZ, +1, false>(v);
+    if (act) {
+#pragma unroll
+        for (int z = 0; z < NZ; ++z) p[z * zstride] = v[dif_pos<PZ>(z)];
+    }
+}
+
+// K3 / K5 for L = L1 x L2 (64 <= L <= 1024): four-step transform of B
+// columns.  Level 1: thread t < L2 of a column holds x[t + L2 n1], n1 < L1,
+// (upper half zero when PIN), DFT over n1, twiddle w_L^(t k1), store to
+// shared memory.  Level 2: thread k1 < L1 holds the L2 values of its row,
+// DFT over n2, X[k1 + L1 k2] (only k2 < L2/2 when POUT).  Shared rows are
+// XOR-swizzled so both levels hit distinct banks.
+template <int L1, int L2, int DIR, bool PIN, bool POUT>
+__global__ void __launch_bounds__(256)
+    k_cols_reg(const float2* in, float2* out, int Hx, int lgB, ColGeom cg, const float2* __restrict__ tw) {
+    constexpr int L = L1 * L2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* S = reinterpret_cast<float2*>(smem_raw);      // [L1][L2][B]
+    const int B = 1 << lgB;
+    const int m = B < 16 ? (16 >> lgB) - 1 : 0;
+    const int b = threadIdx.x & (B - 1), t = threadIdx.x >> lgB;
+    const int col = (blockIdx.x << lgB) + b;
+    const bool act = col < Hx;
+    const int p = blockIdx.y;
+    const int pi = p % cg.n_inner, po = p / cg.n_inner;
+    const float2* ib = in + pi * cg.in_inner + po * cg.in_outer + (act ? col : 0);
+    float2* ob = out + pi * cg.out_inner + po * cg.out_outer + col;
+    if (t < L2) {
+        float2 v[L1];
+        constexpr int NIN = PIN ? L1 / 2 : L1;
+#pragma unroll
+        for (int n1 = 0; n1 < NIN; ++n1) v[n1] = act ? ib[(long)(t + L2 * n1) * cg.rs_in] : make_float2(0.f, 0.f);
+        dif<L1, DIR, PIN>(v);
+#pragma unroll
+        for (int k1 = 0; k1 < L1; ++k1) {
+            float2 y = v[dif_pos<L1>(k1)];
+            if (k1 > 0) {
+                float2 w = tw[t * k1];
+                if (DIR > 0) w.y = -w.y;
+                y = cmul(y, w);
+            }
+            S[((k1 * L2) + (t ^ (k1 & m))) * B + b] = y;
+        }
+    }
+    __syncthreads();
+    if (t < L1) {
+        float2 u[L2];
+#pragma unroll
+        for (int n2 = 0; n2 < L2; ++n2) u[n2] = S[((t * L2) + (n2 ^ (t & m))) * B + b];
+        dif<L2, DIR, false>(u);
+        constexpr int NOUT = POUT ? L2 / 2 : L2;
+        if (act) {
+#pragma unroll
+            for (int k2 = 0; k2 < NOUT; ++k2) ob[(long)(t + L1 * k2) * cg.rs_out] = u[dif_pos<L2>(k2)];
+        }
+    }
+}
+
 // K1 tail: keep the real octant of the transformed component, at precision T.
 template <typename T>
 __global__ void k_extract(const double2* __restrict__ X, int Py, int Hs, int Hx, int Py2, int Pz2,
@@ -377,10 +486,48 @@ int run_xfwd(mm_ctx* ctx, const T* in, long in_ld, int nin, const T* Ms, T ms, l
     return MM_OK;
 }
 
+// FP32 four-step column transform when L = L1 x L2 is one of the tuned sizes
+// and the pruning is the product path's (nin = L/2 forward, nout = L/2 inverse)
+template <int L1, int L2, int DIR>
+int launch_cols_reg(mm_ctx* ctx, const float2* in, float2* out, int nplanes, ColGeom g, const float2* tw) {
+    constexpr int L = L1 * L2;
+    constexpr int B = 4;
+    const size_t smem = (size_t)L * B * sizeof(float2);
+    auto fn = k_cols_reg<L1, L2, DIR, (DIR < 0), (DIR > 0)>;
+    int rc = set_smem(ctx, (const void*)fn, smem);
+    if (rc) return rc;
+    dim3 grid((unsigned)((ctx->Hx + B - 1) / B), (unsigned)nplanes);
+    fn<<<grid, B * (L1 > L2 ? L1 : L2), smem, ctx->stream>>>(in, out, ctx->Hx, 2, g, tw);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+
+template <int DIR>
+int try_cols_reg(mm_ctx* ctx, const float2* in, float2* out, int L, int nplanes, ColGeom g, const float2* tw,
+                 bool* done) {
+    *done = true;
+    switch (L) {
+        case 64: return launch_cols_reg<8, 8, DIR>(ctx, in, out, nplanes, g, tw);
+        case 128: return launch_cols_reg<16, 8, DIR>(ctx, in, out, nplanes, g, tw);
+        case 256: return launch_cols_reg<16, 16, DIR>(ctx, in, out, nplanes, g, tw);
+        case 512: return launch_cols_reg<32, 16, DIR>(ctx, in, out, nplanes, g, tw);
+        case 1024: return launch_cols_reg<32, 32, DIR>(ctx, in, out, nplanes, g, tw);
+        default: *done = false; return MM_OK;
+    }
+}
+
 template <typename T, int DIR>
 int run_cols(mm_ctx* ctx, const C_t<T>* in, C_t<T>* out, int L, int nin, int nout, int nplanes, ColGeom g,
              const C_t<T>* tw) {
     KernelTimer kt(ctx, DIR < 0 ? MM_K_YFWD : MM_K_YINV);
+    if constexpr (sizeof(T) == 4) {
+        const bool product_pruning = DIR < 0 ? (nin == L / 2 && nout == L) : (nin == L && nout == L / 2);
+        if (product_pruning) {
+            bool done = false;
+            int rc = try_cols_reg<DIR>(ctx, in, out, L, nplanes, g, tw, &done);
+            if (done) return rc;
+        }
+    }
     const int B = col_tile(L, sizeof(C_t<T>));
     size_t smem = (size_t)L * B * sizeof(C_t<T>);
     int rc = set_smem(ctx, (const void*)k_cols<T, DIR>, smem);
@@ -390,6 +537,29 @@ int run_cols(mm_ctx* ctx, const C_t<T>* in, C_t<T>* out, int L, int nin, int nou
                                                                           ilog2(B), g, tw);
     MM_LAUNCH_CHECK(ctx);
     return MM_OK;
+}
+
+template <int PZ>
+int launch_zconv_reg_t(mm_ctx* ctx, float2* buf, const float* kern) {
+    constexpr int lgB = 5;   // 32 columns, 3 x 32 threads
+    const size_t smem = (size_t)3 * PZ * (1 << lgB) * sizeof(float2);
+    int rc = set_smem(ctx, (const void*)k_zconv_reg<PZ>, smem);
+    if (rc) return rc;
+    dim3 grid((unsigned)((ctx->Hx + 31) / 32), (unsigned)ctx->Py);
+    k_zconv_reg<PZ><<<grid, 3 << lgB, smem, ctx->stream>>>(buf, kern, ctx->Py, ctx->Hs, ctx->Hx, ctx->Py2, lgB);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+
+int launch_zconv_reg(mm_ctx* ctx, float2* buf, const float* kern) {
+    switch (ctx->Pz) {
+        case 1: return launch_zconv_reg_t<1>(ctx, buf, kern);
+        case 2: return launch_zconv_reg_t<2>(ctx, buf, kern);
+        case 4: return launch_zconv_reg_t<4>(ctx, buf, kern);
+        case 8: return launch_zconv_reg_t<8>(ctx, buf, kern);
+        case 16: return launch_zconv_reg_t<16>(ctx, buf, kern);
+        default: return launch_zconv_reg_t<32>(ctx, buf, kern);
+    }
 }
 
 template <typename T>
@@ -414,7 +584,11 @@ int apply(mm_ctx* ctx, const T* m, T* H) {
         if (rc) return rc;
     }
     // K4
-    {
+    if (sizeof(T) == 4 && ctx->Pz <= 32) {
+        KernelTimer kt(ctx, MM_K_ZCONV);
+        rc = launch_zconv_reg(ctx, (float2*)Bf, (const float*)ctx->kern);
+        if (rc) return rc;
+    } else {
         KernelTimer kt(ctx, MM_K_ZCONV);
         const int Pz = ctx->Pz;
         const int B = z_tile(Pz, sizeof(C));

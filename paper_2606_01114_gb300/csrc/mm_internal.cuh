@@ -24,13 +24,13 @@ template <> struct cx<double> { using type = double2; };
 template <typename C> __host__ __device__ __forceinline__ C cmk(decltype(C{}.x) a, decltype(C{}.x) b) {
     C r; r.x = a; r.y = b; return r;
 }
-template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return cmk<C>(a.x + b.x, a.y + b.y); }
-template <typename C> __device__ __forceinline__ C csub(C a, C b) { return cmk<C>(a.x - b.x, a.y - b.y); }
-template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { return cmk<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { return cmk<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
     return cmk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-template <typename C> __device__ __forceinline__ C cconj(C a) { return cmk<C>(a.x, -a.y); }
-template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C{}.x) s) { return cmk<C>(a.x * s, a.y * s); }
+template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { return cmk<C>(a.x, -a.y); }
+template <typename C> __host__ __device__ __forceinline__ C cscale(C a, decltype(C{}.x) s) { return cmk<C>(a.x * s, a.y * s); }
 
 // --------------------------------------------------------- device control
 // One RKF45/RK4 control block per context, in device memory.
