@@ -353,6 +353,145 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// K2 / K6 for the packed complex length L = L1 x L2 (64 <= L <= 512, L1 >=
+// L2): four-step transform of B rows through shared memory, with the
+// real-to-complex unpacking (forward) or packing (inverse) as a further
+// shared-memory pass.  Level-1 threads (t < L2) hold z[t + L2 n1]; level-2
+// threads (k1 < L1) hold row k1 of the L1 x L2 transpose, XOR-swizzled.
+template <int L1, int L2> __device__ __forceinline__ int xsw(int k1, int n2) {
+    return k1 * L2 + (n2 ^ (k1 & (L2 - 1) & 15));
+}
+
+template <int L1, int L2>
+__global__ void __launch_bounds__(256)
+    k_xfwd_reg(const float* __restrict__ in, const float* __restrict__ Ms, float ms, long ms_rows,
+               float2* __restrict__ out, int Hs, long rows, const float2* __restrict__ twL,
+               const float2* __restrict__ twP) {
+    constexpr int L = L1 * L2, B = 4, NX = L;   // nx real inputs per row, L packed pairs
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* S = reinterpret_cast<float2*>(smem_raw);      // [B][L]
+    const int tid = threadIdx.x;
+    const long r0 = (long)blockIdx.x * B;
+    if (tid < B * L2) {
+        const int t = tid % L2, b = tid / L2;
+        const long r = r0 + b;
+        const bool act = r < rows;
+        const float2* rowp = reinterpret_cast<const float2*>(in + (act ? r : 0) * NX);
+        const float2* msp = Ms ? reinterpret_cast<const float2*>(Ms + ((act ? r : 0) % ms_rows) * NX) : nullptr;
+        float2 v[L1];
+#pragma unroll
+        for (int n1 = 0; n1 < L1 / 2; ++n1) {
+            const int j = t + L2 * n1;
+            float2 a = act ? rowp[j] : make_float2(0.f, 0.f);
+            if (msp) {
+                float2 w = msp[j];
+                a.x *= w.x;
+                a.y *= w.y;
+            } else {
+                a.x *= ms;
+                a.y *= ms;
+            }
+            v[n1] = a;
+        }
+        dif<L1, -1, true>(v);
+#pragma unroll
+        for (int k1 = 0; k1 < L1; ++k1) {
+            float2 y = v[dif_pos<L1>(k1)];
+            if (k1 > 0) y = cmul(y, twL[t * k1]);
+            S[b * L + xsw<L1, L2>(k1, t)] = y;
+        }
+    }
+    __syncthreads();
+    const int k1 = tid % L1, b2 = tid / L1;
+    float2 u[L2];
+#pragma unroll
+    for (int n2 = 0; n2 < L2; ++n2) u[n2] = S[b2 * L + xsw<L1, L2>(k1, n2)];
+    dif<L2, -1, false>(u);
+    __syncthreads();
+#pragma unroll
+    for (int k2 = 0; k2 < L2; ++k2) S[b2 * L + k1 + L1 * k2] = u[dif_pos<L2>(k2)];
+    __syncthreads();
+    // X_k = E_k - i w^k D_k, E, D the even/odd split of the packed spectrum Z
+    for (int idx = tid; idx < B * (L + 1); idx += blockDim.x) {
+        const int b = idx / (L + 1), k = idx - b * (L + 1);
+        const long r = r0 + b;
+        if (r >= rows) continue;
+        const float2 zk = S[b * L + (k & (L - 1))];
+        const float2 zc = cconj(S[b * L + ((L - k) & (L - 1))]);
+        const float2 e = cscale(cadd(zk, zc), 0.5f);
+        const float2 d = cscale(csub(zk, zc), 0.5f);
+        const float2 wd = cmul(twP[k], d);
+        out[r * Hs + k] = make_float2(e.x + wd.y, e.y - wd.x);
+    }
+}
+
+template <int L1, int L2>
+__global__ void __launch_bounds__(256)
+    k_xinv_reg(const float2* __restrict__ in, int Hs, float* __restrict__ out, long rows, float scale,
+               const float2* __restrict__ twL, const float2* __restrict__ twP) {
+    constexpr int L = L1 * L2, B = 4, NX = L;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* S = reinterpret_cast<float2*>(smem_raw);      // [B][L]
+    const int tid = threadIdx.x;
+    const long r0 = (long)blockIdx.x * B;
+    constexpr int U = 4;
+    static_assert(L2 % U == 0, "the row tile must split evenly over the unrolled loads");
+    for (int base = tid; base < B * L; base += U * blockDim.x) {
+        float2 xk[U], xc[U], w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + u * blockDim.x;
+            const int b = idx / L, k = idx % L;
+            const long r = r0 + b;
+            const bool ok = r < rows;
+            xk[u] = ok ? in[r * Hs + k] : make_float2(0.f, 0.f);
+            xc[u] = ok ? in[r * Hs + (L - k)] : make_float2(0.f, 0.f);
+            w[u] = twP[k];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + u * blockDim.x;
+            const float2 c = cconj(xc[u]);
+            const float2 e = cscale(cadd(xk[u], c), 0.5f);
+            const float2 o = cmul(cscale(csub(xk[u], c), 0.5f), cconj(w[u]));   // times exp(+2 pi i k / Px)
+            S[idx] = make_float2(e.x - o.y, e.y + o.x);                         // E + i O
+        }
+    }
+    __syncthreads();
+    float2 v[L1];
+    const int t = tid % L2, b1 = tid / L2;
+    const bool lvl1 = tid < B * L2;
+    if (lvl1) {
+#pragma unroll
+        for (int n1 = 0; n1 < L1; ++n1) v[n1] = S[b1 * L + t + L2 * n1];
+        dif<L1, +1, false>(v);
+    }
+    __syncthreads();
+    if (lvl1) {
+#pragma unroll
+        for (int k1 = 0; k1 < L1; ++k1) {
+            float2 y = v[dif_pos<L1>(k1)];
+            if (k1 > 0) y = cmul(y, cconj(twL[t * k1]));
+            S[b1 * L + xsw<L1, L2>(k1, t)] = y;
+        }
+    }
+    __syncthreads();
+    const int k1 = tid % L1, b2 = tid / L1;
+    const long r = r0 + b2;
+    float2 u[L2];
+#pragma unroll
+    for (int n2 = 0; n2 < L2; ++n2) u[n2] = S[b2 * L + xsw<L1, L2>(k1, n2)];
+    dif<L2, +1, false>(u);
+    if (r < rows) {
+        float2* op = reinterpret_cast<float2*>(out + r * NX);
+#pragma unroll
+        for (int k2 = 0; k2 < L2 / 2; ++k2) {
+            const float2 z = u[dif_pos<L2>(k2)];
+            op[k1 + L1 * k2] = make_float2(z.x * scale, z.y * scale);
+        }
+    }
+}
+
 // K3 / K5 for L = L1 x L2 (64 <= L <= 1024): four-step transform of B
 // columns.  Level 1: thread t < L2 of a column holds x[t + L2 n1], n1 < L1,
 // (upper half zero when PIN), DFT over n1, twiddle w_L^(t k1), store to
@@ -465,6 +604,61 @@ int set_smem(mm_ctx* ctx, const void* fn, size_t bytes) {
     return MM_OK;
 }
 
+template <int L1, int L2>
+int launch_xfwd_reg(mm_ctx* ctx, const float* in, const float* Ms, float ms, long ms_rows, float2* out, long rows,
+                    const float2* twL, const float2* twP) {
+    constexpr int B = 4;
+    const size_t smem = (size_t)B * L1 * L2 * sizeof(float2);
+    int rc = set_smem(ctx, (const void*)k_xfwd_reg<L1, L2>, smem);
+    if (rc) return rc;
+    k_xfwd_reg<L1, L2><<<(unsigned)((rows + B - 1) / B), B * L1, smem, ctx->stream>>>(in, Ms, ms, ms_rows, out,
+                                                                                   ctx->Hs, rows, twL, twP);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+
+int try_xfwd_reg(mm_ctx* ctx, const float* in, const float* Ms, float ms, long ms_rows, float2* out, long rows,
+                 const float2* twL, const float2* twP, int L, bool* done) {
+    *done = true;
+    switch (L) {
+        case 64: return launch_xfwd_reg<8, 8>(ctx, in, Ms, ms, ms_rows, out, rows, twL, twP);
+        case 128: return launch_xfwd_reg<16, 8>(ctx, in, Ms, ms, ms_rows, out, rows, twL, twP);
+        case 256: return launch_xfwd_reg<16, 16>(ctx, in, Ms, ms, ms_rows, out, rows, twL, twP);
+        case 512: return launch_xfwd_reg<32, 16>(ctx, in, Ms, ms, ms_rows, out, rows, twL, twP);
+        default: *done = false; return MM_OK;
+    }
+}
+template <typename T>
+int try_xfwd_reg(mm_ctx*, const T*, const T*, T, long, C_t<T>*, long, const C_t<T>*, const C_t<T>*, int, bool* done) {
+    *done = false;
+    return MM_OK;
+}
+
+template <int L1, int L2>
+int launch_xinv_reg(mm_ctx* ctx, const float2* in, float* out, long rows, float scale, const float2* twL,
+                    const float2* twP) {
+    constexpr int B = 4;
+    const size_t smem = (size_t)B * L1 * L2 * sizeof(float2);
+    int rc = set_smem(ctx, (const void*)k_xinv_reg<L1, L2>, smem);
+    if (rc) return rc;
+    k_xinv_reg<L1, L2><<<(unsigned)((rows + B - 1) / B), B * L1, smem, ctx->stream>>>(in, ctx->Hs, out, rows, scale,
+                                                                                   twL, twP);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+
+int try_xinv_reg(mm_ctx* ctx, const float2* in, float* out, long rows, float scale, const float2* twL,
+                 const float2* twP, int L, bool* done) {
+    *done = true;
+    switch (L) {
+        case 64: return launch_xinv_reg<8, 8>(ctx, in, out, rows, scale, twL, twP);
+        case 128: return launch_xinv_reg<16, 8>(ctx, in, out, rows, scale, twL, twP);
+        case 256: return launch_xinv_reg<16, 16>(ctx, in, out, rows, scale, twL, twP);
+        case 512: return launch_xinv_reg<32, 16>(ctx, in, out, rows, scale, twL, twP);
+        default: *done = false; return MM_OK;
+    }
+}
+
 // x-forward over `rows` rows
 template <typename T>
 int run_xfwd(mm_ctx* ctx, const T* in, long in_ld, int nin, const T* Ms, T ms, long ms_rows, C_t<T>* out,
@@ -476,6 +670,13 @@ int run_xfwd(mm_ctx* ctx, const T* in, long in_ld, int nin, const T* Ms, T ms, l
         return MM_OK;
     }
     const int L = Px / 2;
+    if constexpr (sizeof(T) == 4) {
+        if (in_ld == L && nin == L && L >= 64) {
+            bool done = false;
+            int rc = try_xfwd_reg(ctx, in, Ms, ms, ms_rows, out, rows, twL, twP, L, &done);
+            if (done) return rc;
+        }
+    }
     const int B = x_rows_per_block(L);
     size_t smem = (size_t)L * B * sizeof(C_t<T>);
     int rc = set_smem(ctx, (const void*)k_xfwd<T>, smem);
@@ -616,6 +817,15 @@ int apply(mm_ctx* ctx, const T* m, T* H) {
         MM_LAUNCH_CHECK(ctx);
     } else {
         const int L = ctx->Lx;
+        if constexpr (sizeof(T) == 4) {
+            bool done = false;
+            if (L >= 64) {
+                rc = try_xinv_reg(ctx, (const float2*)xin, (float*)H, rows, (float)scale,
+                                  (const float2*)table<T>(ctx, ctx->tw.off_lx), (const float2*)table<T>(ctx, ctx->tw.off_px),
+                                  L, &done);
+                if (done) return rc;
+            }
+        }
         const int B = x_rows_per_block(L);
         size_t smem = (size_t)L * B * sizeof(C);
         rc = set_smem(ctx, (const void*)k_xinv<T>, smem);
