@@ -175,6 +175,42 @@ int mm_kernel_time(mm_ctx* ctx, int kernel, double* total_ms, long* launches);
  * last integration call.  Any pointer may be NULL. */
 int mm_step_stats(const mm_ctx* ctx, long* accepted, long* rejected, double* t, double* dt);
 
+/* ---- Adjoints (gradients with respect to m and the per-cell Ms) ------------
+ * The paper names automatic differentiation for inverse problems as a
+ * property of its PyTorch base (Introduction); these are hand-written
+ * vector-Jacobian products of Eq. 1, 2 and 4 for that use.  Cotangents and
+ * gradients are device arrays of the path precision: vector fields
+ * [3][nz][ny][nx], gMs [nz][ny][nx] (accumulated: gMs += ..., zero it
+ * first).  The per-cell Ms used is the context's (mm_set_material_fields),
+ * else the uniform value.  The first adjoint call allocates a workspace of
+ * 14 vector fields kept by the context. */
+
+/* gm = (dH_demag/dm)^T g = Ms (-N * g); gMs += m . (-N * g) (gMs nullable).
+ * The Newell operator is symmetric and even, hence self-adjoint. */
+int mm_demag_vjp(mm_ctx* ctx, const void* g, const void* m, void* gm, void* gMs);
+
+/* gm = (dH_ex/dm)^T g = E(g / Ms), E the symmetric exchange stencil;
+ * gMs += -g . H_ex(m) / Ms (gMs nullable). */
+int mm_exchange_vjp(mm_ctx* ctx, const void* g, const void* m, void* gm, void* gMs);
+
+/* One classic RK4 step m1 = u/|u|, u = m0 + dt sum b_s k_s (Eq. 1 with the
+ * full effective field): lam holds dL/dm1 on entry and dL/dm0 on return;
+ * gMs += (dm1/dMs)^T lam.  The stage states are recomputed from m0. */
+int mm_rk4_step_vjp(mm_ctx* ctx, const void* m0, double dt, void* lam, void* gMs);
+
+/* nsteps fixed RK4 steps of m in place without host synchronisation
+ * between steps; waits for the stream at the end. */
+int mm_rk4_trajectory(mm_ctx* ctx, void* m, double dt, long nsteps);
+
+/* Reverse pass of mm_rk4_trajectory from m0: lam = dL/dm_N on entry,
+ * dL/dm_0 on return; gMs += dL/dMs.  Checkpoints the state every
+ * checkpoint_every steps (<= 0: ceil(sqrt(nsteps))) and recomputes each
+ * segment before pulling back through it, so memory is about
+ * (nsteps / K + K) states; that store is allocated for the call and freed
+ * before it returns. */
+int mm_rk4_trajectory_vjp(mm_ctx* ctx, const void* m0, double dt, long nsteps, void* lam, void* gMs,
+                          long checkpoint_every);
+
 /* Energies without a context and without any device allocation.
  *
  * The paper has no counterpart: this entry point exists for callers that

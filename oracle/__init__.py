@@ -12,6 +12,8 @@ GPU library computes, written from the paper's equations:
                  field of Eq. 2, uniaxial anisotropy, Zeeman, the LLG right-hand
                  side of Eq. 1, classic RK4 and Fehlberg RKF45 steps (the paper's
                  integrator), energies, torque and relax().
+* ``adjoint``  - gradients of a trajectory loss with respect to the per-cell
+                 Ms by their definition (central differences, Richardson).
 
 It is NOT part of the product.  Only ``tests/``, ``__graft_entry__.smoke()`` and
 ``bench.py``'s CPU-baseline leg may import it.  It imports nothing from the GPU
@@ -20,4 +22,4 @@ package and the GPU package imports nothing from it.  Arrays are float64
 ``[3][nz][ny][nx]`` with x fastest, SI units throughout.
 """
 
-from . import newell, micromag  # noqa: F401
+from . import newell, micromag, adjoint  # noqa: F401

@@ -77,6 +77,11 @@ def _load():
         "mm_kernel_time": (I, [P, I, DP, LP]),
         "mm_step_stats": (I, [P, LP, LP, DP, DP]),
         "mm_energy_noalloc": (I, [I, I, I, D, D, D, I, D, D, D, DP, DP, P, P, DP, P]),
+        "mm_demag_vjp": (I, [P, P, P, P, P]),
+        "mm_exchange_vjp": (I, [P, P, P, P, P]),
+        "mm_rk4_step_vjp": (I, [P, P, D, P, P]),
+        "mm_rk4_trajectory": (I, [P, P, D, L]),
+        "mm_rk4_trajectory_vjp": (I, [P, P, D, L, P, P, L]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -264,6 +269,31 @@ def mm_step_stats(ctx):
     t, dt = ctypes.c_double(0.0), ctypes.c_double(0.0)
     _check(ctx, _load().mm_step_stats(ctx.handle, ctypes.byref(a), ctypes.byref(r), ctypes.byref(t), ctypes.byref(dt)))
     return a.value, r.value, t.value, dt.value
+
+
+def mm_demag_vjp(ctx, g, m, gm, gMs=None):
+    _check(ctx, _load().mm_demag_vjp(ctx.handle, _dev(ctx, g, ctx.shape3, "g"), _dev(ctx, m, ctx.shape3, "m"),
+                                      _dev(ctx, gm, ctx.shape3, "gm"), _dev(ctx, gMs, ctx.shape1, "gMs")))
+
+
+def mm_exchange_vjp(ctx, g, m, gm, gMs=None):
+    _check(ctx, _load().mm_exchange_vjp(ctx.handle, _dev(ctx, g, ctx.shape3, "g"), _dev(ctx, m, ctx.shape3, "m"),
+                                         _dev(ctx, gm, ctx.shape3, "gm"), _dev(ctx, gMs, ctx.shape1, "gMs")))
+
+
+def mm_rk4_step_vjp(ctx, m0, dt, lam, gMs):
+    _check(ctx, _load().mm_rk4_step_vjp(ctx.handle, _dev(ctx, m0, ctx.shape3, "m0"), float(dt),
+                                         _dev(ctx, lam, ctx.shape3, "lam"), _dev(ctx, gMs, ctx.shape1, "gMs")))
+
+
+def mm_rk4_trajectory(ctx, m, dt, nsteps):
+    _check(ctx, _load().mm_rk4_trajectory(ctx.handle, _dev(ctx, m, ctx.shape3, "m"), float(dt), int(nsteps)))
+
+
+def mm_rk4_trajectory_vjp(ctx, m0, dt, nsteps, lam, gMs, checkpoint_every=0):
+    _check(ctx, _load().mm_rk4_trajectory_vjp(ctx.handle, _dev(ctx, m0, ctx.shape3, "m0"), float(dt), int(nsteps),
+                                               _dev(ctx, lam, ctx.shape3, "lam"), _dev(ctx, gMs, ctx.shape1, "gMs"),
+                                               int(checkpoint_every)))
 
 
 def mm_energy_noalloc(n, d, precision, Ms, A, Ku, u, h_ext, m, H_demag, stream=None):

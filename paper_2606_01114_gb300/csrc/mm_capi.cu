@@ -85,7 +85,8 @@ size_t elem(const mm_ctx* ctx) { return ctx->prec == MM_F64 ? sizeof(double) : s
 
 void free_all(mm_ctx* ctx) {
     void* ptrs[] = {ctx->Ms_cell, ctx->A_cell, ctx->kern, ctx->bufA, ctx->bufB, ctx->Hd, ctx->Hs_field,
-                    ctx->m0, ctx->ms[0], ctx->ms[1], ctx->mnext, ctx->kptrs, ctx->ctl, ctx->tw.f64, ctx->tw.f32};
+                    ctx->m0, ctx->ms[0], ctx->ms[1], ctx->mnext, ctx->kptrs, ctx->ctl, ctx->tw.f64, ctx->tw.f32,
+                    ctx->adj};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (void* p : ctx->k)
@@ -185,6 +186,15 @@ int device_status(mm_ctx* ctx) {
 }
 
 }  // namespace
+
+int ctl_reset_push(mm_ctx* ctx, double t, double dt, double t_max, double tol) {
+    int rc = sync(ctx);
+    if (rc) return rc;
+    reset_ctl(ctx->ctl_host, t, dt, t_max, tol);
+    return push_ctl(ctx);
+}
+int ctl_pull(mm_ctx* ctx) { return pull_ctl(ctx); }
+
 }  // namespace mm
 
 using namespace mm;

@@ -763,18 +763,20 @@ int launch_zconv_reg(mm_ctx* ctx, float2* buf, const float* kern) {
     }
 }
 
+// unit = true: the same convolution with Ms = 1 everywhere (H = -N * m),
+// the transpose needed by the adjoint
 template <typename T>
-int apply(mm_ctx* ctx, const T* m, T* H) {
+int apply(mm_ctx* ctx, const T* m, T* H, bool unit = false) {
     using C = C_t<T>;
     const long plane = (long)ctx->ny * ctx->nx;
     const long rows = 3L * ctx->nz * ctx->ny;
     C* A = (C*)ctx->bufA;
     C* Bf = (C*)ctx->bufB;
     C* xout = ctx->Py == 1 ? Bf : A;
-    const T* Ms = ctx->has_Ms_cell ? (const T*)ctx->Ms_cell : nullptr;
+    const T* Ms = (ctx->has_Ms_cell && !unit) ? (const T*)ctx->Ms_cell : nullptr;
     int rc;
     // K2
-    rc = run_xfwd<T>(ctx, m, ctx->nx, ctx->nx, Ms, (T)ctx->Ms, (long)ctx->nz * ctx->ny, xout, rows,
+    rc = run_xfwd<T>(ctx, m, ctx->nx, ctx->nx, Ms, unit ? (T)1 : (T)ctx->Ms, (long)ctx->nz * ctx->ny, xout, rows,
                      table<T>(ctx, ctx->tw.off_lx), table<T>(ctx, ctx->tw.off_px), ctx->Px);
     if (rc) return rc;
     (void)plane;
@@ -909,6 +911,11 @@ int demag_setup(mm_ctx* ctx) {
 int demag_apply(mm_ctx* ctx, const void* m, void* H) {
     if (ctx->prec == MM_F64) return apply<double>(ctx, (const double*)m, (double*)H);
     return apply<float>(ctx, (const float*)m, (float*)H);
+}
+
+int demag_apply_unit(mm_ctx* ctx, const void* g, void* H) {
+    if (ctx->prec == MM_F64) return apply<double>(ctx, (const double*)g, (double*)H, true);
+    return apply<float>(ctx, (const float*)g, (float*)H, true);
 }
 
 }  // namespace mm

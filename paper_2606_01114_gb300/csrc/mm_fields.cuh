@@ -1,0 +1,119 @@
+// Per-cell field helpers shared by the LLG kernels and their adjoints:
+// material parameters, the 6-point exchange stencil (Eq. 2 for unit m),
+// anisotropy + Zeeman, and the LLG right-hand side (Eq. 1 for unit m).
+#pragma once
+
+#include "mm_internal.cuh"
+
+namespace mm {
+
+// --------------------------------------------------------- parameters
+template <typename T> struct Params {
+    int nx, ny, nz;
+    long N;
+    const T* Ms_cell;   // nullable
+    const T* A_cell;    // nullable
+    T Ms, A;
+    T cx, cy, cz;       // 2 / (mu0 d^2) per axis
+    T anis;             // 2 Ku / mu0
+    T ux, uy, uz;
+    T hx, hy, hz;
+    T pref;             // -gamma / (1 + alpha^2)
+    T alpha;
+};
+
+template <typename T>
+inline Params<T> make_params(const mm_ctx* ctx) {
+    Params<T> p;
+    p.nx = ctx->nx;
+    p.ny = ctx->ny;
+    p.nz = ctx->nz;
+    p.N = ctx->N;
+    p.Ms_cell = ctx->has_Ms_cell ? (const T*)ctx->Ms_cell : nullptr;
+    p.A_cell = ctx->has_A_cell ? (const T*)ctx->A_cell : nullptr;
+    p.Ms = (T)ctx->Ms;
+    p.A = (T)ctx->A;
+    p.cx = (T)(2.0 / (kMu0 * ctx->dx * ctx->dx));
+    p.cy = (T)(2.0 / (kMu0 * ctx->dy * ctx->dy));
+    p.cz = (T)(2.0 / (kMu0 * ctx->dz * ctx->dz));
+    p.anis = (T)(2.0 * ctx->Ku / kMu0);
+    p.ux = (T)ctx->u[0];
+    p.uy = (T)ctx->u[1];
+    p.uz = (T)ctx->u[2];
+    p.hx = (T)ctx->hext[0];
+    p.hy = (T)ctx->hext[1];
+    p.hz = (T)ctx->hext[2];
+    p.pref = (T)(-kGamma / (1.0 + ctx->alpha * ctx->alpha));
+    p.alpha = (T)ctx->alpha;
+    return p;
+}
+
+template <typename T> struct V3 { T x, y, z; };
+
+template <typename T>
+__device__ __forceinline__ V3<T> load3(const T* __restrict__ a, long i, long N) {
+    return {a[i], a[i + N], a[i + 2 * N]};
+}
+template <typename T>
+__device__ __forceinline__ void store3(T* __restrict__ a, long i, long N, V3<T> v) {
+    a[i] = v.x;
+    a[i + N] = v.y;
+    a[i + 2 * N] = v.z;
+}
+
+// exchange field at cell i (x, y, z) of state m; Msi > 0
+template <typename T>
+__device__ __forceinline__ V3<T> exchange_at(const Params<T>& p, const T* __restrict__ m, long i, int x, int y,
+                                             int z, V3<T> mi, T Msi) {
+    const T Ai = p.A_cell ? p.A_cell[i] : p.A;
+    T ax = 0, ay = 0, az = 0;
+    auto nb = [&](long j, T c) {
+        T Msj = p.Ms_cell ? p.Ms_cell[j] : p.Ms;
+        if (Msj == (T)0) return;
+        T Ah;
+        if (p.A_cell) {
+            T Aj = p.A_cell[j];
+            T s = Ai + Aj;
+            Ah = s > (T)0 ? (T)2 * Ai * Aj / s : (T)0;
+        } else {
+            Ah = p.A;
+        }
+        T w = Ah * c;
+        ax += w * (m[j] - mi.x);
+        ay += w * (m[j + p.N] - mi.y);
+        az += w * (m[j + 2 * p.N] - mi.z);
+    };
+    const long sx = 1, sy = p.nx, sz = (long)p.nx * p.ny;
+    if (x > 0) nb(i - sx, p.cx);
+    if (x < p.nx - 1) nb(i + sx, p.cx);
+    if (y > 0) nb(i - sy, p.cy);
+    if (y < p.ny - 1) nb(i + sy, p.cy);
+    if (z > 0) nb(i - sz, p.cz);
+    if (z < p.nz - 1) nb(i + sz, p.cz);
+    T inv = (T)1 / Msi;
+    return {ax * inv, ay * inv, az * inv};
+}
+
+// anisotropy + Zeeman at a magnetic cell
+template <typename T>
+__device__ __forceinline__ V3<T> local_at(const Params<T>& p, V3<T> mi, T Msi) {
+    T mu = mi.x * p.ux + mi.y * p.uy + mi.z * p.uz;
+    T k = p.anis / Msi * mu;
+    return {k * p.ux + p.hx, k * p.uy + p.hy, k * p.uz + p.hz};
+}
+
+template <typename T>
+__device__ __forceinline__ V3<T> llg_rhs(const Params<T>& p, V3<T> m, V3<T> H) {
+    V3<T> a = {m.y * H.z - m.z * H.y, m.z * H.x - m.x * H.z, m.x * H.y - m.y * H.x};   // m x H
+    V3<T> b = {m.y * a.z - m.z * a.y, m.z * a.x - m.x * a.z, m.x * a.y - m.y * a.x};   // m x (m x H)
+    return {p.pref * (a.x + p.alpha * b.x), p.pref * (a.y + p.alpha * b.y), p.pref * (a.z + p.alpha * b.z)};
+}
+
+__device__ __forceinline__ void decompose(long i, int nx, int ny, int& x, int& y, int& z) {
+    x = (int)(i % nx);
+    long r = i / nx;
+    y = (int)(r % ny);
+    z = (int)(r / ny);
+}
+
+}  // namespace mm

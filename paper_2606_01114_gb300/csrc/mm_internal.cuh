@@ -92,6 +92,7 @@ struct mm_ctx {
     void* mnext;              // [3][N] accepted-candidate state
     void* k[6];               // [3][N] RK stage slopes
     void* kptrs;              // device copy of k[0..5]
+    void* adj;                // adjoint workspace (14 fields of [3][N]), allocated on first use
     mm::Control* ctl;         // device control block
     mm::Control* ctl_host;    // pinned host mirror
     double* newell_host;      // [6][nz][ny][nx] real-space tensor (host copy)
@@ -154,6 +155,7 @@ struct KernelTimer {
 // ----- demag (mm_demag.cu)
 int demag_setup(mm_ctx* ctx);                          // K1: Newell tensor -> k-space octant
 int demag_apply(mm_ctx* ctx, const void* m, void* H);  // K2..K6
+int demag_apply_unit(mm_ctx* ctx, const void* g, void* H);  // same with Ms = 1 (adjoint)
 
 // ----- Newell (mm_newell.cu)
 // Fills the FP64 real-space padded grid [Pz][Py][Px] of component c (0..5)
@@ -171,5 +173,8 @@ int rk_stage(mm_ctx* ctx, int method, int s, const void* m_in, const void* m0, v
 int rk_controller(mm_ctx* ctx, int method);            // accept / reject, dt
 int rk_commit(mm_ctx* ctx, void* m0);                  // m0 <- mnext if accepted
 int check_finite_launch(mm_ctx* ctx, const void* m);            // flags ctl->status
+// host helpers shared with the adjoint (mm_capi.cu)
+int ctl_reset_push(mm_ctx* ctx, double t, double dt, double t_max, double tol);
+int ctl_pull(mm_ctx* ctx);
 
 }  // namespace mm
