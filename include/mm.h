@@ -211,6 +211,21 @@ int mm_rk4_trajectory(mm_ctx* ctx, void* m, double dt, long nsteps);
 int mm_rk4_trajectory_vjp(mm_ctx* ctx, const void* m0, double dt, long nsteps, void* lam, void* gMs,
                           long checkpoint_every);
 
+/* ---- Tensor-core split-precision DFT stage ----------------------------------
+ * The paper's FFTs run in FP64/FP32 through cuFFT; this is the precision
+ * variant of its radix stages: a 32-point DFT as a real GEMM on the
+ * 5th-generation tensor cores, FP32 operands split into hi + lo parts of the
+ * tensor-core type and multiplied as hi.hi + hi.lo + lo.hi with FP32
+ * accumulation (about 21 significant bits for TF32, 16 for BF16). */
+enum { MM_TC_TF32 = 1, MM_TC_BF16 = 2 };
+
+/* out[l][k] = sum_n in[l][n] exp(direction 2 pi i n k / 32) for nlines
+ * lines of 32 complex FP32 values (interleaved re, im; device arrays,
+ * in != out).  direction -1 or +1.  Waits for the stream.  Errors:
+ * INVALID_ARG, CUDA, TIMEOUT (a bounded tensor-core wait gave up; read with
+ * mm_last_error(NULL)). */
+int mm_dft32_tc(const void* in, void* out, long nlines, int mode, int direction, void* stream);
+
 /* Energies without a context and without any device allocation.
  *
  * The paper has no counterpart: this entry point exists for callers that

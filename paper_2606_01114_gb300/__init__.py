@@ -27,6 +27,7 @@ MM_ERR_DT_UNDERFLOW = -4
 MM_ERR_NOT_CONVERGED = -5
 MM_ERR_TIMEOUT = -6
 MM_ERR_NOMEM = -7
+MM_TC_TF32, MM_TC_BF16 = 1, 2
 # kernel classes for mm_kernel_time
 MM_K_XFWD, MM_K_YFWD, MM_K_ZCONV, MM_K_YINV, MM_K_XINV, MM_K_STAGE, MM_K_CONTROL, MM_K_REDUCE = range(8)
 MM_K_COUNT = 8
@@ -82,6 +83,7 @@ def _load():
         "mm_rk4_step_vjp": (I, [P, P, D, P, P]),
         "mm_rk4_trajectory": (I, [P, P, D, L]),
         "mm_rk4_trajectory_vjp": (I, [P, P, D, L, P, P, L]),
+        "mm_dft32_tc": (I, [P, P, L, I, I, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -294,6 +296,21 @@ def mm_rk4_trajectory_vjp(ctx, m0, dt, nsteps, lam, gMs, checkpoint_every=0):
     _check(ctx, _load().mm_rk4_trajectory_vjp(ctx.handle, _dev(ctx, m0, ctx.shape3, "m0"), float(dt), int(nsteps),
                                                _dev(ctx, lam, ctx.shape3, "lam"), _dev(ctx, gMs, ctx.shape1, "gMs"),
                                                int(checkpoint_every)))
+
+
+def mm_dft32_tc(inp, out, mode=MM_TC_TF32, direction=-1, stream=None):
+    """Batched 32-point complex DFT on tensor cores (split hi + lo operands).
+    inp, out: complex64 CUDA tensors of shape (nlines, 32)."""
+    for name, t in (("inp", inp), ("out", out)):
+        if not getattr(t, "is_cuda", False) or str(t.dtype).split(".")[-1] != "complex64" or t.shape[-1] != 32:
+            raise ValueError(f"{name} must be a complex64 CUDA tensor with 32 values per line")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    lib = _load()
+    rc = lib.mm_dft32_tc(ctypes.c_void_p(inp.data_ptr()), ctypes.c_void_p(out.data_ptr()), int(inp.numel() // 32),
+                         int(mode), int(direction), _stream_ptr(stream))
+    if rc != MM_OK:
+        raise MMError(rc, lib.mm_last_error(None).decode())
 
 
 def mm_energy_noalloc(n, d, precision, Ms, A, Ku, u, h_ext, m, H_demag, stream=None):

@@ -1,0 +1,289 @@
+// Tensor-core split-precision DFT stages (5th-generation tensor cores,
+// tcgen05 with the accumulator in tensor memory).
+//
+// A batch of 32-point complex DFTs is one real GEMM: the 128 lines of a tile
+// are the rows of A (interleaved re/im, K = 64), B is the real form of the
+// 32 x 32 DFT matrix (N = 64 outputs: Re X_k = sum c x.re - s x.im,
+// Im X_k = sum s x.re + c x.im with c + i s = exp(dir 2 pi i n k / 32)).
+// FP32 operands are split into hi + lo parts of the tensor-core type
+// (TF32: round to 10 mantissa bits; BF16: round to 7) and the product is
+// formed as hi.hi + hi.lo + lo.hi with FP32 accumulation, which keeps
+// about twice the operand type's bits.  One elected thread issues the MMAs
+// (operands in shared memory, canonical K-major layout without swizzle),
+// tcgen05.commit signals an mbarrier, every warp reads its 32 accumulator
+// rows back with tcgen05.ld.  Every wait is bounded: on a timeout the block
+// raises the library's device status and frees its tensor memory.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <mutex>
+
+#include "mm_internal.cuh"
+
+namespace mm {
+namespace {
+
+constexpr int kTcLines = 128;    // M: lines per tile
+constexpr int kTcK = 64;         // K: 32 complex inputs
+constexpr int kTcN = 64;         // N: 32 complex outputs
+constexpr long kTcWaitLimit = 1L << 22;
+
+// DFT matrix of each mode and direction in the GEMM's B layout
+// ([N][K] values, hi and lo parts), built once per device
+__device__ float g_dft_f32[2][2][kTcN * kTcK];            // [dir][hi/lo]
+__device__ __nv_bfloat16 g_dft_bf16[2][2][kTcN * kTcK];
+__device__ int g_tc_status;
+
+bool g_tables_ready[64] = {false};
+std::mutex g_tables_mutex;
+
+__device__ __forceinline__ float tf32_round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__global__ void k_init_dft_tables() {
+    for (int idx = threadIdx.x + blockIdx.x * blockDim.x; idx < 2 * kTcN * kTcK; idx += blockDim.x * gridDim.x) {
+        const int d = idx / (kTcN * kTcK), e = idx % (kTcN * kTcK);
+        const int j = e / kTcK, kk = e % kTcK;        // output j (2k + part), input kk (2n + part)
+        const int k = j >> 1, n = kk >> 1;
+        const double dir = d == 0 ? -1.0 : 1.0;
+        double c, s;
+        sincospi(dir * 2.0 * (double)((n * k) % 32) / 32.0, &s, &c);
+        double v;
+        if ((j & 1) == 0) v = (kk & 1) == 0 ? c : -s;   // Re X_k
+        else v = (kk & 1) == 0 ? s : c;                  // Im X_k
+        const float hi32 = tf32_round((float)v);
+        g_dft_f32[d][0][e] = hi32;
+        g_dft_f32[d][1][e] = tf32_round((float)(v - (double)hi32));
+        const __nv_bfloat16 hb = __float2bfloat16_rn((float)v);
+        g_dft_bf16[d][0][e] = hb;
+        g_dft_bf16[d][1][e] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(hb)));
+    }
+}
+
+// byte offset of element (r, k) in the canonical K-major layout without
+// swizzle: 8-row x 16-byte core matrices, adjacent in K (LBO = 128 B), row
+// groups SBO = (K / elements per 16 B) * 128 B apart
+template <int ES> __device__ __forceinline__ int kmajor_off(int r, int k, int K) {
+    constexpr int KC = 16 / ES;
+    return (r >> 3) * ((K / KC) * 128) + (k / KC) * 128 + (r & 7) * 16 + (k % KC) * ES;
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// kind::tf32 or kind::f16 (bf16) instruction descriptor: D f32, K-major A and B
+template <bool TF32> __device__ __forceinline__ uint32_t instr_desc() {
+    const uint32_t fmt = TF32 ? 2u : 1u;
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcLines >> 4) << 24);
+}
+
+template <bool TF32>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if constexpr (TF32) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+    for (long it = 0; it < kTcWaitLimit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(mbar), "r"(phase)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// Shared memory of one tile: A hi/lo [128 x 64], B hi/lo [64 x 64] (element
+// size ES), the mbarrier and the tensor-memory address.
+template <int ES> struct TcSmem {
+    static constexpr int A_BYTES = kTcLines * kTcK * ES;
+    static constexpr int B_BYTES = kTcN * kTcK * ES;
+    static constexpr int BYTES = 2 * A_BYTES + 2 * B_BYTES + 64;
+};
+
+// Batched 32-point DFT of `nlines` contiguous lines of 32 float2 values.
+template <bool TF32>
+__global__ void __launch_bounds__(kTcLines) k_dft32_tc(const float2* __restrict__ in, float2* __restrict__ out,
+                                                       long nlines, int dir_index) {
+    constexpr int ES = TF32 ? 4 : 2;
+    using S = TcSmem<ES>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* a_hi = smem;
+    unsigned char* a_lo = smem + S::A_BYTES;
+    unsigned char* b_hi = smem + 2 * S::A_BYTES;
+    unsigned char* b_lo = b_hi + S::B_BYTES;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(b_lo + S::B_BYTES);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(b_lo + S::B_BYTES + 16);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t mbar_a = (uint32_t)__cvta_generic_to_shared(mbar);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(tmem_slot)),
+                     "r"(kTcN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_a));
+
+    // B: the DFT matrix, [N][K] in the K-major layout
+    for (int e = tid; e < kTcN * kTcK; e += blockDim.x) {
+        const int j = e / kTcK, kk = e % kTcK;
+        const int o = kmajor_off<ES>(j, kk, kTcK);
+        if constexpr (TF32) {
+            *reinterpret_cast<float*>(b_hi + o) = g_dft_f32[dir_index][0][e];
+            *reinterpret_cast<float*>(b_lo + o) = g_dft_f32[dir_index][1][e];
+        } else {
+            *reinterpret_cast<__nv_bfloat16*>(b_hi + o) = g_dft_bf16[dir_index][0][e];
+            *reinterpret_cast<__nv_bfloat16*>(b_lo + o) = g_dft_bf16[dir_index][1][e];
+        }
+    }
+    // A: one line per thread, split into hi + lo
+    const long line = (long)blockIdx.x * kTcLines + tid;
+    for (int n = 0; n < 32; ++n) {
+        float2 v = line < nlines ? in[line * 32 + n] : make_float2(0.f, 0.f);
+        const float xs[2] = {v.x, v.y};
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+            const int o = kmajor_off<ES>(tid, 2 * n + part, kTcK);
+            const float x = xs[part];
+            if constexpr (TF32) {
+                const float h = tf32_round(x);
+                *reinterpret_cast<float*>(a_hi + o) = h;
+                *reinterpret_cast<float*>(a_lo + o) = tf32_round(x - h);
+            } else {
+                const __nv_bfloat16 h = __float2bfloat16_rn(x);
+                *reinterpret_cast<__nv_bfloat16*>(a_hi + o) = h;
+                *reinterpret_cast<__nv_bfloat16*>(a_lo + o) = __float2bfloat16_rn(x - __bfloat162float(h));
+            }
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (tid == 0) {
+        const uint32_t idesc = instr_desc<TF32>();
+        const uint32_t sbo_a = (kTcK / (16 / ES)) * 128, sbo_b = sbo_a;
+        const uint32_t A[2] = {(uint32_t)__cvta_generic_to_shared(a_hi), (uint32_t)__cvta_generic_to_shared(a_lo)};
+        const uint32_t Bm[2] = {(uint32_t)__cvta_generic_to_shared(b_hi), (uint32_t)__cvta_generic_to_shared(b_lo)};
+        // hi.hi + hi.lo + lo.hi
+        const int pa[3] = {0, 0, 1}, pb[3] = {0, 1, 0};
+        constexpr int KMMA = TF32 ? 8 : 16;          // K per instruction: 32 bytes = 2 core matrices
+        uint32_t acc = 0;
+        for (int p = 0; p < 3; ++p) {
+            for (int kc = 0; kc < kTcK / KMMA; ++kc) {
+                const uint64_t ad = smem_desc(A[pa[p]] + kc * 256, 128, sbo_a);
+                const uint64_t bd = smem_desc(Bm[pb[p]] + kc * 256, 128, sbo_b);
+                mma<TF32>(tmem, ad, bd, idesc, acc);
+                acc = 1;
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_a)
+                     : "memory");
+    }
+    const bool ok = mbar_wait(mbar_a, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!ok) {
+        if ((tid & 31) == 0) atomicCAS(&g_tc_status, 0, (int)MM_ERR_TIMEOUT);
+    } else {
+        uint32_t r[64];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+            "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+            "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+              "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+              "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+              "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+              "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (line < nlines) {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) out[line * 32 + k] = make_float2(__uint_as_float(r[2 * k]), __uint_as_float(r[2 * k + 1]));
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcN));
+}
+
+int ensure_tables(int dev, cudaStream_t st) {
+    if (dev < 0 || dev >= 64) return fail(nullptr, MM_ERR_INVALID_ARG, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_tables_mutex);
+    if (!g_tables_ready[dev]) {
+        k_init_dft_tables<<<16, 256, 0, st>>>();
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return fail(nullptr, MM_ERR_CUDA, "DFT table setup: %s", cudaGetErrorString(e));
+        g_tables_ready[dev] = true;
+    }
+    return MM_OK;
+}
+
+}  // namespace
+}  // namespace mm
+
+using namespace mm;
+
+extern "C" int mm_dft32_tc(const void* in, void* out, long nlines, int mode, int direction, void* stream) {
+    if (!in || !out || nlines < 0) return fail(nullptr, MM_ERR_INVALID_ARG, "mm_dft32_tc: bad arguments");
+    if (mode != MM_TC_TF32 && mode != MM_TC_BF16) return fail(nullptr, MM_ERR_INVALID_ARG, "mm_dft32_tc: bad mode");
+    if (direction != -1 && direction != 1) return fail(nullptr, MM_ERR_INVALID_ARG, "mm_dft32_tc: direction is -1 or 1");
+    if (nlines == 0) return MM_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    cudaError_t e = st ? cudaStreamGetDevice(st, &dev) : cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaSetDevice(dev);
+    if (e != cudaSuccess) return fail(nullptr, MM_ERR_CUDA, "mm_dft32_tc: %s", cudaGetErrorString(e));
+    int rc = ensure_tables(dev, st);
+    if (rc) return rc;
+    const int zero = 0;
+    e = cudaMemcpyToSymbolAsync(g_tc_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+    const unsigned grid = (unsigned)((nlines + kTcLines - 1) / kTcLines);
+    const int dir_index = direction < 0 ? 0 : 1;
+    if (e == cudaSuccess) {
+        if (mode == MM_TC_TF32) {
+            const int bytes = TcSmem<4>::BYTES;
+            e = cudaFuncSetAttribute(k_dft32_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+            if (e == cudaSuccess) k_dft32_tc<true><<<grid, kTcLines, bytes, st>>>((const float2*)in, (float2*)out, nlines, dir_index);
+        } else {
+            const int bytes = TcSmem<2>::BYTES;
+            e = cudaFuncSetAttribute(k_dft32_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+            if (e == cudaSuccess) k_dft32_tc<false><<<grid, kTcLines, bytes, st>>>((const float2*)in, (float2*)out, nlines, dir_index);
+        }
+        if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    int status = 0;
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbolAsync(&status, g_tc_status, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(nullptr, MM_ERR_CUDA, "mm_dft32_tc: %s", cudaGetErrorString(e));
+    if (status) return fail(nullptr, status, "mm_dft32_tc: tensor-core wait timed out");
+    return MM_OK;
+}
