@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--fft-mode", choices=["fp32", "tf32", "bf16"], default="fp32",
+                    help="FP32 context only: tensor-core split-precision y passes")
     ap.add_argument("--workload", choices=["film512"], default="film512")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -271,6 +273,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     ctx = mm.mm_init_mesh(*n, *d, precision=prec, stream=stream)
     mm.mm_set_material(ctx, w["Ms"], w["A"], w["alpha"], w["Ku"])
+    if args.fft_mode != "fp32":
+        mm.mm_set_fft_mode(ctx, mm.MM_TC_TF32 if args.fft_mode == "tf32" else mm.MM_TC_BF16)
     m_host = wl.vortex(n, d, noise=0.05, seed=1)
     m = torch.tensor(m_host, dtype=tdtype, device="cuda")
 
@@ -377,6 +381,7 @@ def run_ours(args):
                                    "A 1.3e-11 J/m, alpha 0.5, seeded vortex + 5% noise, adaptive RKF45 tol 1e-5 "
                                    "via relax()",
                        "parallelism": "replicas" if world > 1 else "single GPU",
+                       "fft": args.fft_mode,
                        "l2": "no flush: one field evaluation moves ~1.9 GB, far above the 129 MB L2"},
             "llg_mcell_steps_per_s": mcell,
             "accepted_steps": accepted, "rejected_trials": rejected, "field_evals": evals,

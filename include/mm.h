@@ -226,6 +226,16 @@ enum { MM_TC_TF32 = 1, MM_TC_BF16 = 2 };
  * mm_last_error(NULL)). */
 int mm_dft32_tc(const void* in, void* out, long nlines, int mode, int direction, void* stream);
 
+/* FFT arithmetic of an MM_F32 context's demag passes: 0 = plain FP32
+ * (default), MM_TC_TF32 or MM_TC_BF16 = the y passes of length 512 or 1024
+ * run their 32-point level on tensor cores with split operands (the other
+ * passes stay FP32).  INVALID_ARG for an MM_F64 context. */
+int mm_set_fft_mode(mm_ctx* ctx, int mode);
+
+/* MM_OK, or MM_ERR_TIMEOUT if a tensor-core wait of this device gave up
+ * since the last check (waits for the stream). */
+int mm_tc_status(mm_ctx* ctx);
+
 /* Energies without a context and without any device allocation.
  *
  * The paper has no counterpart: this entry point exists for callers that

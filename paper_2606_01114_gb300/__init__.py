@@ -84,6 +84,8 @@ def _load():
         "mm_rk4_trajectory": (I, [P, P, D, L]),
         "mm_rk4_trajectory_vjp": (I, [P, P, D, L, P, P, L]),
         "mm_dft32_tc": (I, [P, P, L, I, I, P]),
+        "mm_set_fft_mode": (I, [P, I]),
+        "mm_tc_status": (I, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -296,6 +298,15 @@ def mm_rk4_trajectory_vjp(ctx, m0, dt, nsteps, lam, gMs, checkpoint_every=0):
     _check(ctx, _load().mm_rk4_trajectory_vjp(ctx.handle, _dev(ctx, m0, ctx.shape3, "m0"), float(dt), int(nsteps),
                                                _dev(ctx, lam, ctx.shape3, "lam"), _dev(ctx, gMs, ctx.shape1, "gMs"),
                                                int(checkpoint_every)))
+
+
+def mm_set_fft_mode(ctx, mode):
+    """0 = plain FP32 passes, MM_TC_TF32 / MM_TC_BF16 = tensor-core y passes."""
+    _check(ctx, _load().mm_set_fft_mode(ctx.handle, int(mode)))
+
+
+def mm_tc_status(ctx):
+    _check(ctx, _load().mm_tc_status(ctx.handle))
 
 
 def mm_dft32_tc(inp, out, mode=MM_TC_TF32, direction=-1, stream=None):

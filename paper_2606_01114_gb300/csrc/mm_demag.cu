@@ -165,12 +165,6 @@ __global__ void k_x1inv(const C_t<T>* __restrict__ in, int Hs, T* __restrict__ o
 // adjacent columns (kx) of one plane, loads nin rows (rest zero), transforms
 // length L = 2^lgL, stores nout rows.  Plane p: inner index p % n_inner,
 // outer p / n_inner.
-struct ColGeom {
-    long rs_in, rs_out;                // row strides (elements)
-    int n_inner;
-    long in_inner, in_outer, out_inner, out_outer;
-};
-
 template <typename T, int DIR>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_cols(const C_t<T>* in, C_t<T>* out, int lgL, int nin, int nout, int Hx, int lgB, ColGeom cg,
                        const C_t<T>* __restrict__ tw) {
@@ -723,6 +717,8 @@ int run_cols(mm_ctx* ctx, const C_t<T>* in, C_t<T>* out, int L, int nin, int nou
     KernelTimer kt(ctx, DIR < 0 ? MM_K_YFWD : MM_K_YINV);
     if constexpr (sizeof(T) == 4) {
         const bool product_pruning = DIR < 0 ? (nin == L / 2 && nout == L) : (nin == L && nout == L / 2);
+        if (product_pruning && ctx->fft_mode != 0 && (L == 512 || L == 1024))
+            return tc_cols(ctx, in, out, L, DIR, nplanes, g, tw);
         if (product_pruning) {
             bool done = false;
             int rc = try_cols_reg<DIR>(ctx, in, out, L, nplanes, g, tw, &done);

@@ -74,6 +74,7 @@ struct mm_ctx {
     int Hx;                   // kept x frequencies (nx + 1, or 1)
     int Hs;                   // row stride of k-space arrays (Hx rounded up to 16)
     int Py2, Pz2;             // Py/2+1, Pz/2+1: stored kernel octant extents
+    int fft_mode;             // 0 plain FP32 passes, MM_TC_TF32 / MM_TC_BF16: tensor-core y passes
 
     // material
     double Ms, A, alpha, Ku, u[3], hext[3];
@@ -151,6 +152,20 @@ struct KernelTimer {
     KernelTimer(mm_ctx* c, int kind);
     ~KernelTimer();
 };
+
+// Column transform geometry shared by the plain and tensor-core y passes:
+// row strides, planes p = (p % n_inner, p / n_inner) with their strides.
+struct ColGeom {
+    long rs_in, rs_out;
+    int n_inner;
+    long in_inner, in_outer, out_inner, out_outer;
+};
+
+// Four-step column transform with the 32-point level on tensor cores
+// (mm_tc.cu); L = 512 or 1024; forward (dir -1) reads L/2 rows, inverse
+// (dir +1) writes L/2 rows.  Returns MM_OK or an error code.
+int tc_cols(mm_ctx* ctx, const float2* in, float2* out, int L, int dir, int nplanes, ColGeom g, const float2* tw);
+int tc_prepare(mm_ctx* ctx);
 
 // ----- demag (mm_demag.cu)
 int demag_setup(mm_ctx* ctx);                          // K1: Newell tensor -> k-space octant

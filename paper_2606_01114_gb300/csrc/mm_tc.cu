@@ -18,7 +18,7 @@
 #include <cmath>
 #include <mutex>
 
-#include "mm_internal.cuh"
+#include "mm_regfft.cuh"
 
 namespace mm {
 namespace {
@@ -234,6 +234,170 @@ __global__ void __launch_bounds__(kTcLines) k_dft32_tc(const float2* __restrict_
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcN));
 }
 
+// Four-step column transform of length L = 32 L2 for B = 128 / L2 adjacent
+// columns: level 1 (rows (t2, b), 32-point DFT over n1 of x[t2 + L2 n1]) is
+// one tensor-core GEMM of the 128 rows; on read-back each row is twiddled
+// by w_L^(t2 k1) and transposed through shared memory; level 2 (thread
+// (k1, b), L2-point DFT over n2 in registers) writes X[k1 + 32 k2].
+// PIN: the upper half of the input rows is zero (K = 32 real inputs);
+// POUT: only the lower half of the output rows is written.
+template <int L2, int DIR, bool PIN, bool POUT, bool TF32>
+__global__ void __launch_bounds__(32 * (128 / L2))
+    k_cols_tc(const float2* in, float2* out, int Hx, ColGeom cg, const float2* __restrict__ tw) {
+    constexpr int B = 128 / L2, L = 32 * L2;
+    constexpr int ES = TF32 ? 4 : 2;
+    constexpr int KA = PIN ? 32 : 64;
+    using S = TcSmem<ES>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* a_hi = smem;
+    unsigned char* a_lo = smem + S::A_BYTES;
+    unsigned char* b_hi = smem + 2 * S::A_BYTES;
+    unsigned char* b_lo = b_hi + S::B_BYTES;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(b_lo + S::B_BYTES);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(b_lo + S::B_BYTES + 16);
+    float2* T = reinterpret_cast<float2*>(smem);            // level-2 transpose, reuses A after the MMA
+    static_assert(L * B * 8 <= 2 * S::A_BYTES, "transpose must fit in the A operand space");
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int m = B < 16 ? 16 / B - 1 : 0;
+    const uint32_t mbar_a = (uint32_t)__cvta_generic_to_shared(mbar);
+    const int dir_index = DIR < 0 ? 0 : 1;
+    const int col0 = blockIdx.x * B;
+    const int p = blockIdx.y;
+    const int pi = p % cg.n_inner, po = p / cg.n_inner;
+    const float2* ib = in + pi * cg.in_inner + po * cg.in_outer;
+    float2* ob = out + pi * cg.out_inner + po * cg.out_outer;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(tmem_slot)),
+                     "r"(kTcN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_a));
+    for (int e = tid; e < kTcN * kTcK; e += blockDim.x) {
+        const int j = e / kTcK, kk = e % kTcK;
+        if (kk >= KA) continue;
+        const int o = kmajor_off<ES>(j, kk, kTcK);
+        if constexpr (TF32) {
+            *reinterpret_cast<float*>(b_hi + o) = g_dft_f32[dir_index][0][e];
+            *reinterpret_cast<float*>(b_lo + o) = g_dft_f32[dir_index][1][e];
+        } else {
+            *reinterpret_cast<__nv_bfloat16*>(b_hi + o) = g_dft_bf16[dir_index][0][e];
+            *reinterpret_cast<__nv_bfloat16*>(b_lo + o) = g_dft_bf16[dir_index][1][e];
+        }
+    }
+    const int t2 = tid / B, bb = tid % B;
+    const bool act = col0 + bb < Hx;
+    if (tid < kTcLines) {
+        float2 v[KA / 2];
+#pragma unroll
+        for (int n1 = 0; n1 < KA / 2; ++n1)
+            v[n1] = act ? ib[(long)(t2 + L2 * n1) * cg.rs_in + col0 + bb] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int n1 = 0; n1 < KA / 2; ++n1) {
+            const float xs[2] = {v[n1].x, v[n1].y};
+#pragma unroll
+            for (int part = 0; part < 2; ++part) {
+                const int o = kmajor_off<ES>(tid, 2 * n1 + part, kTcK);
+                if constexpr (TF32) {
+                    const float h = tf32_round(xs[part]);
+                    *reinterpret_cast<float*>(a_hi + o) = h;
+                    *reinterpret_cast<float*>(a_lo + o) = tf32_round(xs[part] - h);
+                } else {
+                    const __nv_bfloat16 h = __float2bfloat16_rn(xs[part]);
+                    *reinterpret_cast<__nv_bfloat16*>(a_hi + o) = h;
+                    *reinterpret_cast<__nv_bfloat16*>(a_lo + o) = __float2bfloat16_rn(xs[part] - __bfloat162float(h));
+                }
+            }
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    if (tid == 0) {
+        const uint32_t idesc = instr_desc<TF32>();
+        const uint32_t sbo = (kTcK / (16 / ES)) * 128;
+        const uint32_t A[2] = {(uint32_t)__cvta_generic_to_shared(a_hi), (uint32_t)__cvta_generic_to_shared(a_lo)};
+        const uint32_t Bm[2] = {(uint32_t)__cvta_generic_to_shared(b_hi), (uint32_t)__cvta_generic_to_shared(b_lo)};
+        const int pa[3] = {0, 0, 1}, pb[3] = {0, 1, 0};
+        constexpr int KMMA = TF32 ? 8 : 16;
+        uint32_t acc = 0;
+        for (int q = 0; q < 3; ++q)
+            for (int kc = 0; kc < KA / KMMA; ++kc) {
+                mma<TF32>(tmem, smem_desc(A[pa[q]] + kc * 256, 128, sbo), smem_desc(Bm[pb[q]] + kc * 256, 128, sbo), idesc,
+                          acc);
+                acc = 1;
+            }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_a)
+                     : "memory");
+    }
+    const bool ok = mbar_wait(mbar_a, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!ok && (tid & 31) == 0) atomicCAS(&g_tc_status, 0, (int)MM_ERR_TIMEOUT);
+    if (ok && tid < kTcLines) {
+        uint32_t r[64];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+            "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+            "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+              "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+              "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+              "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+              "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        // all MMA reads of A are complete (mbarrier), so T may overwrite A
+#pragma unroll
+        for (int k1 = 0; k1 < 32; ++k1) {
+            float2 y = make_float2(__uint_as_float(r[2 * k1]), __uint_as_float(r[2 * k1 + 1]));
+            if (k1 > 0) {
+                float2 w = tw[t2 * k1];
+                if (DIR > 0) w.y = -w.y;
+                y = cmul(y, w);
+            }
+            T[((k1 * L2) + (t2 ^ (k1 & m))) * B + bb] = y;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcN));
+    {
+        const int k1 = tid / B, b2 = tid % B;
+        const bool act2 = col0 + b2 < Hx;
+        float2 u[L2];
+#pragma unroll
+        for (int n2 = 0; n2 < L2; ++n2) u[n2] = T[((k1 * L2) + (n2 ^ (k1 & m))) * B + b2];
+        dif<L2, DIR, false>(u);
+        constexpr int NOUT = POUT ? L2 / 2 : L2;
+        if (act2 && ok) {
+#pragma unroll
+            for (int k2 = 0; k2 < NOUT; ++k2) ob[(long)(k1 + 32 * k2) * cg.rs_out + col0 + b2] = u[dif_pos<L2>(k2)];
+        }
+    }
+}
+
+template <int L2, int DIR, bool TF32>
+int launch_cols_tc(mm_ctx* ctx, const float2* in, float2* out, int nplanes, ColGeom g, const float2* tw) {
+    constexpr int B = 128 / L2;
+    const int bytes = TcSmem<TF32 ? 4 : 2>::BYTES;
+    auto fn = k_cols_tc<L2, DIR, (DIR < 0), (DIR > 0), TF32>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return fail(ctx, MM_ERR_CUDA, "tensor-core pass setup: %s", cudaGetErrorString(e));
+    dim3 grid((unsigned)((ctx->Hx + B - 1) / B), (unsigned)nplanes);
+    fn<<<grid, 32 * B, bytes, ctx->stream>>>(in, out, ctx->Hx, g, tw);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+
 int ensure_tables(int dev, cudaStream_t st) {
     if (dev < 0 || dev >= 64) return fail(nullptr, MM_ERR_INVALID_ARG, "device index %d out of range", dev);
     std::lock_guard<std::mutex> lock(g_tables_mutex);
@@ -248,9 +412,50 @@ int ensure_tables(int dev, cudaStream_t st) {
 }
 
 }  // namespace
+
+int tc_prepare(mm_ctx* ctx) { return ensure_tables(ctx->device, ctx->stream); }
+
+int tc_cols(mm_ctx* ctx, const float2* in, float2* out, int L, int dir, int nplanes, ColGeom g, const float2* tw) {
+    const bool tf32 = ctx->fft_mode == MM_TC_TF32;
+    if (L == 512) {
+        if (dir < 0) return tf32 ? launch_cols_tc<16, -1, true>(ctx, in, out, nplanes, g, tw)
+                                 : launch_cols_tc<16, -1, false>(ctx, in, out, nplanes, g, tw);
+        return tf32 ? launch_cols_tc<16, 1, true>(ctx, in, out, nplanes, g, tw)
+                    : launch_cols_tc<16, 1, false>(ctx, in, out, nplanes, g, tw);
+    }
+    if (dir < 0) return tf32 ? launch_cols_tc<32, -1, true>(ctx, in, out, nplanes, g, tw)
+                             : launch_cols_tc<32, -1, false>(ctx, in, out, nplanes, g, tw);
+    return tf32 ? launch_cols_tc<32, 1, true>(ctx, in, out, nplanes, g, tw)
+                : launch_cols_tc<32, 1, false>(ctx, in, out, nplanes, g, tw);
+}
+
 }  // namespace mm
 
 using namespace mm;
+
+extern "C" int mm_set_fft_mode(mm_ctx* ctx, int mode) {
+    if (!ctx) return fail(nullptr, MM_ERR_INVALID_ARG, "ctx is NULL");
+    if (mode != 0 && mode != MM_TC_TF32 && mode != MM_TC_BF16) return fail(ctx, MM_ERR_INVALID_ARG, "bad FFT mode %d", mode);
+    if (mode != 0 && ctx->prec != MM_F32) return fail(ctx, MM_ERR_INVALID_ARG, "tensor-core passes need an MM_F32 context");
+    MM_BIND(ctx);
+    if (mode != 0) {
+        int rc = tc_prepare(ctx);
+        if (rc) return fail(ctx, rc, "%s", mm_last_error(nullptr));
+    }
+    ctx->fft_mode = mode;
+    return MM_OK;
+}
+
+extern "C" int mm_tc_status(mm_ctx* ctx) {
+    if (!ctx) return fail(nullptr, MM_ERR_INVALID_ARG, "ctx is NULL");
+    MM_BIND(ctx);
+    int status = 0;
+    cudaError_t e = cudaMemcpyFromSymbolAsync(&status, g_tc_status, sizeof(int), 0, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return fail(ctx, MM_ERR_CUDA, "%s", cudaGetErrorString(e));
+    if (status) return fail(ctx, status, "a tensor-core wait timed out");
+    return MM_OK;
+}
 
 extern "C" int mm_dft32_tc(const void* in, void* out, long nlines, int mode, int direction, void* stream) {
     if (!in || !out || nlines < 0) return fail(nullptr, MM_ERR_INVALID_ARG, "mm_dft32_tc: bad arguments");

@@ -35,3 +35,36 @@ def test_dft32_tc_matches_fft(mode, direction, nlines):
     xs = x.astype(np.complex64).astype(np.complex128)
     ref = np.fft.fft(xs, axis=1) if direction < 0 else np.fft.ifft(xs, axis=1) * 32
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < BOUND[mode]
+
+
+TC_MESHES = [((32, 256, 4), (2e-9, 2e-9, 2e-9)), ((16, 512, 2), (2.5e-9, 2.5e-9, 3e-9))]
+
+
+@pytest.mark.parametrize("mode", [mm.MM_TC_TF32, mm.MM_TC_BF16], ids=["tf32", "bf16"])
+@pytest.mark.parametrize("n,d", TC_MESHES)
+def test_demag_with_tensor_core_y_passes(n, d, mode):
+    """Demag with the y passes on tensor cores against the float64 oracle.
+    TF32 hi + lo keeps the field within the FP32 tolerance (1e-5); BF16
+    hi + lo (about 16 bits) within 1e-4."""
+    import workloads as wl
+    from oracle import micromag
+    p = micromag.Problem(n, d)
+    m = wl.random_unit(n, seed=3)
+    ctx = mm.mm_init_mesh(*n, *d, precision=mm.MM_F32)
+    mm.mm_set_fft_mode(ctx, mode)
+    md = torch.tensor(m, dtype=torch.float32, device="cuda")
+    H = torch.empty_like(md)
+    mm.mm_demag_field(ctx, md, H)
+    mm.mm_tc_status(ctx)
+    ref = p.demag_fft(m)
+    err = np.linalg.norm(H.double().cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert err < (1e-5 if mode == mm.MM_TC_TF32 else 1e-4), err
+    mm.mm_destroy(ctx)
+
+
+def test_fft_mode_rejected_for_fp64():
+    ctx = mm.mm_init_mesh(8, 8, 2, 1e-9, 1e-9, 1e-9, precision=mm.MM_F64)
+    with pytest.raises(mm.MMError) as e:
+        mm.mm_set_fft_mode(ctx, mm.MM_TC_TF32)
+    assert e.value.code == mm.MM_ERR_INVALID_ARG
+    mm.mm_destroy(ctx)
