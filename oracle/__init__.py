@@ -14,6 +14,8 @@ GPU library computes, written from the paper's equations:
                  integrator), energies, torque and relax().
 * ``adjoint``  - gradients of a trajectory loss with respect to the per-cell
                  Ms by their definition (central differences, Richardson).
+* ``fno``      - the demag surrogate network in float64 PyTorch (CPU), with
+                 gradients by autograd, for checking the GPU kernels.
 
 It is NOT part of the product.  Only ``tests/``, ``__graft_entry__.smoke()`` and
 ``bench.py``'s CPU-baseline leg may import it.  It imports nothing from the GPU
@@ -22,4 +24,4 @@ package and the GPU package imports nothing from it.  Arrays are float64
 ``[3][nz][ny][nx]`` with x fastest, SI units throughout.
 """
 
-from . import newell, micromag, adjoint  # noqa: F401
+from . import newell, micromag, adjoint, fno  # noqa: F401
