@@ -236,6 +236,48 @@ int mm_set_fft_mode(mm_ctx* ctx, int mode);
  * since the last check (waits for the stream). */
 int mm_tc_status(mm_ctx* ctx);
 
+/* ---- Fourier-neural-operator surrogate of the demag field ------------------
+ * Not in the paper: a learned stand-in for Eq. 4 on 2-D films (nz = 1), used
+ * inside relax() with the exact field recomputed every k steps.  Network:
+ * lift 3 -> width (1x1), `layers` Fourier layers a = W v + b +
+ * IDFT(R . DFT v) on the retained modes kx < modes, ky < modes or
+ * ky >= ny - modes, GELU between layers, projection width -> 3 (1x1).
+ * Maps m [B][3][ny][nx] to h = H_demag / Ms [B][3][ny][nx] (FP32 device
+ * arrays).  Activations are stored as BF16 (store_bf16 = 1) or FP32, every
+ * contraction accumulates in FP32; parameters are FP32.  Errors go to
+ * mm_last_error(NULL). */
+typedef struct mm_fno mm_fno;
+int mm_fno_create(mm_fno** out, int nx, int ny, int width, int modes, int layers, int store_bf16,
+                  int max_batch, unsigned long long seed, void* stream);
+void mm_fno_destroy(mm_fno* f);
+long mm_fno_num_params(const mm_fno* f);
+/* h = FNO(m) for `batch` samples; keeps the activations for mm_fno_backward. */
+int mm_fno_forward(mm_fno* f, const void* m, void* h, int batch);
+/* Accumulates dL/dparams (gradients += ...) for cotangent dh of the last
+ * forward call on the same m. */
+int mm_fno_backward(mm_fno* f, const void* m, const void* dh, int batch);
+int mm_fno_zero_grad(mm_fno* f);
+int mm_fno_adam_step(mm_fno* f, double lr, double beta1, double beta2, double eps, long step);
+/* Mean over samples of |h - target|^2 / |target|^2 (*loss_out, nullable,
+ * waits for the stream); dh (nullable) receives its gradient. */
+int mm_fno_loss(mm_fno* f, const void* h, const void* target, void* dh, int batch, double* loss_out);
+/* Host copies: read parameters / gradients (nullable), or set parameters
+ * from host_set (nullable); mm_fno_num_params floats each. */
+int mm_fno_params(mm_fno* f, float* host_params, float* host_grads, const float* host_set);
+/* Output multiplier (1 for training; Ms when the output stands in for H). */
+int mm_fno_set_output_scale(mm_fno* f, double scale);
+
+/* relax() with the surrogate: every k_exact accepted-step window starts
+ * with the exact demag field of the current state, the surrogate's field of
+ * the same state and their relative L2 residual; if the residual is at most
+ * `bound` the window's RKF45 stages take their demag field from the
+ * surrogate, else from the exact FFT convolution (a fallback).  Stops like
+ * mm_relax (torque from the exact field at window starts).  MM_F32 context,
+ * nz = 1, uniform Ms, surrogate of the same grid.  stats (nullable, 3
+ * longs): exact demag evaluations, surrogate evaluations, fallbacks. */
+int mm_relax_surrogate(mm_ctx* ctx, mm_fno* f, void* m, double t_max, double torque_tol, long max_steps,
+                       int k_exact, double bound, double* t_out, long* steps_out, long* stats);
+
 /* Energies without a context and without any device allocation.
  *
  * The paper has no counterpart: this entry point exists for callers that

@@ -86,6 +86,18 @@ def _load():
         "mm_dft32_tc": (I, [P, P, L, I, I, P]),
         "mm_set_fft_mode": (I, [P, I]),
         "mm_tc_status": (I, [P]),
+        "mm_fno_create": (I, [ctypes.POINTER(P), I, I, I, I, I, I, I, ctypes.c_ulonglong, P]),
+        "mm_fno_destroy": (None, [P]),
+        "mm_fno_num_params": (L, [P]),
+        "mm_fno_forward": (I, [P, P, P, I]),
+        "mm_fno_backward": (I, [P, P, P, I]),
+        "mm_fno_zero_grad": (I, [P]),
+        "mm_fno_adam_step": (I, [P, D, D, D, D, L]),
+        "mm_fno_loss": (I, [P, P, P, P, I, DP]),
+        "mm_fno_params": (I, [P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                              ctypes.POINTER(ctypes.c_float)]),
+        "mm_fno_set_output_scale": (I, [P, D]),
+        "mm_relax_surrogate": (I, [P, P, P, D, D, L, I, D, DP, LP, LP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -345,6 +357,100 @@ def mm_energy_noalloc(n, d, precision, Ms, A, Ku, u, h_ext, m, H_demag, stream=N
     if rc != MM_OK:
         raise MMError(rc, lib.mm_last_error(None).decode())
     return np.array(E[:])
+
+
+class FNO:
+    """Handle of an ``mm_fno`` (created by ``mm_fno_create``)."""
+
+    def __init__(self, handle, nx, ny, max_batch):
+        self.handle, self.nx, self.ny, self.max_batch = handle, nx, ny, max_batch
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.mm_fno_destroy(self.handle)
+            self.handle = None
+
+
+def _fcheck(rc):
+    if rc != MM_OK:
+        raise MMError(rc, _load().mm_last_error(None).decode())
+
+
+def _f32(t, shape, name):
+    if not getattr(t, "is_cuda", False) or str(t.dtype).split(".")[-1] != "float32" or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    if tuple(t.shape[-3:]) != tuple(shape):
+        raise ValueError(f"{name} must end in shape {shape}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def mm_fno_create(nx, ny, width=32, modes=16, layers=4, store_bf16=True, max_batch=16, seed=0, stream=None):
+    h = ctypes.c_void_p()
+    _fcheck(_load().mm_fno_create(ctypes.byref(h), int(nx), int(ny), int(width), int(modes), int(layers),
+                                  1 if store_bf16 else 0, int(max_batch), int(seed), _stream_ptr(stream)))
+    return FNO(h, nx, ny, max_batch)
+
+
+def mm_fno_destroy(f):
+    if f.handle:
+        _load().mm_fno_destroy(f.handle)
+        f.handle = None
+
+
+def mm_fno_num_params(f):
+    return int(_load().mm_fno_num_params(f.handle))
+
+
+def mm_fno_forward(f, m, h):
+    _fcheck(_load().mm_fno_forward(f.handle, _f32(m, (3, f.ny, f.nx), "m"), _f32(h, (3, f.ny, f.nx), "h"),
+                                   int(m.numel() // (3 * f.nx * f.ny))))
+
+
+def mm_fno_backward(f, m, dh):
+    _fcheck(_load().mm_fno_backward(f.handle, _f32(m, (3, f.ny, f.nx), "m"), _f32(dh, (3, f.ny, f.nx), "dh"),
+                                    int(m.numel() // (3 * f.nx * f.ny))))
+
+
+def mm_fno_zero_grad(f):
+    _fcheck(_load().mm_fno_zero_grad(f.handle))
+
+
+def mm_fno_adam_step(f, lr, beta1=0.9, beta2=0.999, eps=1e-8, step=1):
+    _fcheck(_load().mm_fno_adam_step(f.handle, float(lr), float(beta1), float(beta2), float(eps), int(step)))
+
+
+def mm_fno_loss(f, h, target, dh=None):
+    out = ctypes.c_double(0.0)
+    _fcheck(_load().mm_fno_loss(f.handle, _f32(h, (3, f.ny, f.nx), "h"), _f32(target, (3, f.ny, f.nx), "target"),
+                                None if dh is None else _f32(dh, (3, f.ny, f.nx), "dh"),
+                                int(h.numel() // (3 * f.nx * f.ny)), ctypes.byref(out)))
+    return out.value
+
+
+def mm_fno_params(f, set_params=None):
+    """Returns (params, grads) as float32 numpy arrays; sets parameters first if given."""
+    n = mm_fno_num_params(f)
+    p = np.empty(n, dtype=np.float32)
+    g = np.empty(n, dtype=np.float32)
+    fp = ctypes.POINTER(ctypes.c_float)
+    s = None if set_params is None else np.ascontiguousarray(set_params, dtype=np.float32)
+    _fcheck(_load().mm_fno_params(f.handle, p.ctypes.data_as(fp), g.ctypes.data_as(fp),
+                                  None if s is None else s.ctypes.data_as(fp)))
+    return p, g
+
+
+def mm_fno_set_output_scale(f, scale):
+    _fcheck(_load().mm_fno_set_output_scale(f.handle, float(scale)))
+
+
+def mm_relax_surrogate(ctx, f, m, t_max, torque_tol=1e-4, max_steps=1000000, k_exact=10, bound=1e-3):
+    """Returns (t, accepted_steps, exact_evals, surrogate_evals, fallbacks)."""
+    tt, ss = ctypes.c_double(0.0), ctypes.c_long(0)
+    st = (ctypes.c_long * 3)()
+    _check(ctx, _load().mm_relax_surrogate(ctx.handle, f.handle, _dev(ctx, m, ctx.shape3, "m"), float(t_max),
+                                           float(torque_tol), int(max_steps), int(k_exact), float(bound),
+                                           ctypes.byref(tt), ctypes.byref(ss), st))
+    return tt.value, ss.value, st[0], st[1], st[2]
 
 
 def from_paper_layout(m_xyz3):

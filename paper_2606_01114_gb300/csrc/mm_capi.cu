@@ -162,6 +162,20 @@ void reset_ctl(Control* c, double t, double dt, double t_max, double tol) {
     c->tol = tol;
 }
 
+// demag field of a stage state: the exact convolution, or the surrogate
+// (output scaled by Ms) when one is attached for this window
+mm_fno* g_stage_surrogate = nullptr;
+long g_surrogate_evals = 0, g_exact_evals = 0;
+
+int stage_field(mm_ctx* ctx, const void* m_in) {
+    if (g_stage_surrogate) {
+        ++g_surrogate_evals;
+        return mm_fno_forward(g_stage_surrogate, m_in, ctx->Hd, 1);
+    }
+    ++g_exact_evals;
+    return demag_apply(ctx, m_in, ctx->Hd);
+}
+
 // one trial step from m (RK4 writes m in place; RKF45 writes mnext and commits)
 int trial(mm_ctx* ctx, void* m, int method) {
     const int S = method == MM_RK4 ? 4 : 6;
@@ -169,7 +183,7 @@ int trial(mm_ctx* ctx, void* m, int method) {
     for (int s = 0; s < S; ++s) {
         const void* m_in = s == 0 ? m : ctx->ms[s % 2];
         void* m_out = s < S - 1 ? ctx->ms[(s + 1) % 2] : (method == MM_RK4 ? m : ctx->mnext);
-        if ((rc = demag_apply(ctx, m_in, ctx->Hd))) return rc;
+        if ((rc = stage_field(ctx, m_in))) return rc;
         if ((rc = rk_stage(ctx, method, s, m_in, m, m_out))) return rc;
     }
     if ((rc = rk_controller(ctx, method))) return rc;
@@ -430,6 +444,75 @@ int mm_relax(mm_ctx* ctx, void* m, double t_max, double torque_tol, long max_ste
         for (int k = 0; k < kCheck; ++k, ++attempts)
             if ((rc = trial(ctx, m, MM_RKF45))) return rc;
     }
+}
+
+int mm_relax_surrogate(mm_ctx* ctx, mm_fno* f, void* m, double t_max, double torque_tol, long max_steps,
+                       int k_exact, double bound, double* t_out, long* steps_out, long* stats) {
+    if (!ctx) return fail(nullptr, MM_ERR_INVALID_ARG, "ctx is NULL");
+    if (!f || !m || k_exact < 1 || !(t_max > 0) || !(torque_tol >= 0) || max_steps < 0 || !(bound >= 0))
+        return fail(ctx, MM_ERR_INVALID_ARG, "surrogate, m, k_exact >= 1, t_max > 0, bounds >= 0 required");
+    if (ctx->prec != MM_F32 || ctx->nz != 1 || ctx->has_Ms_cell)
+        return fail(ctx, MM_ERR_INVALID_ARG, "the surrogate serves MM_F32 films (nz = 1) of uniform Ms");
+    int fnx, fny;
+    fno_grid(f, &fnx, &fny);
+    if (fnx != ctx->nx || fny != ctx->ny) return fail(ctx, MM_ERR_INVALID_ARG, "surrogate grid differs from the mesh");
+    MM_BIND(ctx);
+    int rc;
+    if ((rc = sync(ctx))) return rc;
+    if ((rc = mm_fno_set_output_scale(f, ctx->Ms))) return rc;
+    const cudaStream_t fno_stream = fno_swap_stream(f, ctx->stream);
+    reset_ctl(ctx->ctl_host, 0.0, std::fmin(1e-14, t_max), t_max, 1e-5);
+    if ((rc = push_ctl(ctx))) return rc;
+    if ((rc = check_finite_launch(ctx, m))) return rc;
+    long exact0 = g_exact_evals, sur0 = g_surrogate_evals, fallbacks = 0, attempts = 0;
+    const long max_attempts = 20 * (max_steps + 10);
+    rc = MM_OK;
+    while (rc == MM_OK) {
+        // window start: exact field, surrogate field, residual, torque
+        MM_CUDA_CHECK(ctx, cudaMemsetAsync(&ctx->ctl->torque_bits, 0, sizeof(unsigned long long), ctx->stream));
+        ++g_exact_evals;
+        if ((rc = demag_apply(ctx, m, ctx->Hs_field))) break;
+        ++g_surrogate_evals;
+        if ((rc = mm_fno_forward(f, m, ctx->Hd, 1))) break;
+        double loss = 0.0;
+        if ((rc = mm_fno_loss(f, ctx->Hd, ctx->Hs_field, nullptr, 1, &loss))) break;
+        if ((rc = torque_launch(ctx, m, ctx->Hs_field))) break;
+        if ((rc = pull_ctl(ctx))) break;
+        if ((rc = device_status(ctx))) break;
+        const Control* c = ctx->ctl_host;
+        double tq;
+        unsigned long long bits = c->torque_bits;
+        memcpy(&tq, &bits, sizeof(tq));
+        if (t_out) *t_out = c->t;
+        if (steps_out) *steps_out = (long)c->steps;
+        if (tq <= torque_tol || c->done) break;
+        if (c->steps >= max_steps || attempts >= max_attempts) {
+            rc = fail(ctx, MM_ERR_NOT_CONVERGED, "surrogate relax stopped after %lld steps, torque %.3e",
+                      (long long)c->steps, tq);
+            break;
+        }
+        const bool use = std::sqrt(loss) <= bound;
+        if (!use) ++fallbacks;
+        g_stage_surrogate = use ? f : nullptr;
+        const long target = c->steps + k_exact;
+        for (int k = 0; k < 4 * k_exact && rc == MM_OK; ++k, ++attempts) {
+            rc = trial(ctx, m, MM_RKF45);
+            if (rc == MM_OK && (k + 1) % k_exact == 0) {
+                if ((rc = pull_ctl(ctx))) break;
+                if (ctx->ctl_host->steps >= target || ctx->ctl_host->done || ctx->ctl_host->status) break;
+            }
+        }
+        g_stage_surrogate = nullptr;
+    }
+    g_stage_surrogate = nullptr;
+    fno_swap_stream(f, fno_stream);
+    mm_fno_set_output_scale(f, 1.0);
+    if (stats) {
+        stats[0] = g_exact_evals - exact0;
+        stats[1] = g_surrogate_evals - sur0;
+        stats[2] = fallbacks;
+    }
+    return rc;
 }
 
 int mm_energy(mm_ctx* ctx, const void* m, double E_out[4]) {

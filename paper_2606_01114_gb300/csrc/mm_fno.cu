@@ -1,0 +1,601 @@
+// Fourier neural operator surrogate of the demagnetisation field (2-D films,
+// nz = 1) with hand-written forward, backward and Adam kernels.
+//
+// Network (per sample, grid NY x NX, width W, MX x MY retained modes with
+// kx in [0, MX) and ky in [0, MX) U [NY - MX, NY)):
+//   v0 = P m + p                                  (lift, 1x1, 3 -> W)
+//   a_l = W_l v_l + b_l + IDFT_x IDFT_y (R_l . DFT_y DFT_x v_l),
+//   v_{l+1} = GELU(a_l) (l < L-1), v_L = a_{L-1}
+//   h = Q v_L + q                                 (projection, 1x1, W -> 3)
+// trained on h = H_demag / Ms.  DFT_x keeps kx < MX of the real input;
+// IDFT_x is the matching truncated real inverse
+// z(x) = sum_kx c_kx Re(u_kx e^{2 pi i kx x / NX}) / (NX NY), c_0 = 1, else 2.
+// R_l[co][ci][ky][kx] are complex per-mode channel mixers.  Activations are
+// stored as BF16 (or FP32) and every contraction accumulates in FP32.
+//
+// Backward uses the adjoints under the real inner product: the adjoint of a
+// complex-linear map is its conjugate transpose (DFT_y <-> IDFT_y with
+// flipped sign, T = R S -> dS = R^H dT, dR = dT S^H), the adjoint of
+// DFT_x on real input is Re(sum dA e^{+i theta}), that of IDFT_x is
+// c_kx / (NX NY) sum_x g e^{-i theta}.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <vector>
+
+#include "mm_internal.cuh"
+
+struct mm_fno {
+    int nx, ny, W, M, L, store_bf16, max_batch, device;
+    cudaStream_t stream;
+    long P;             // pixels
+    int MY, K;          // ky count (2 M), modes per channel (MY * M)
+    long nparams;
+    float* params;      // master weights, FP32
+    float* grads;
+    float* adam_m;
+    float* adam_v;
+    // offsets into params
+    long o_P, o_p, o_Q, o_q;
+    std::vector<long> o_W, o_b, o_R;
+    // activations (storage type) and spectral buffers
+    void* v;            // [L+1][B][W][P]  v_0 .. v_L
+    void* a;            // [L][B][W][P]    pre-activations
+    float2* S;          // [L][B][W][K]    retained spectra of v_l
+    float2* A;          // [B][W][NY][M]   x-transform scratch
+    float2* T;          // [B][W][K]
+    float2* U;          // [B][W][NY][M]
+    void* dv;           // [2][B][W][P]    ping-pong cotangents (FP32)
+    float2* twx;        // [M][NX]  e^{-2 pi i kx x / NX}
+    float2* twy;        // [MY][NY] e^{-2 pi i ky y / NY}
+    double* red;        // loss reduction scratch [2][B]
+    float out_scale;    // multiply h by this on output (Ms inside relax)
+    std::string err;
+};
+
+namespace mm {
+namespace {
+
+template <typename S> __device__ __forceinline__ float ld(const S* p, long i);
+template <> __device__ __forceinline__ float ld<float>(const float* p, long i) { return p[i]; }
+template <> __device__ __forceinline__ float ld<__nv_bfloat16>(const __nv_bfloat16* p, long i) {
+    return __bfloat162float(p[i]);
+}
+template <typename S> __device__ __forceinline__ void st(S* p, long i, float v);
+template <> __device__ __forceinline__ void st<float>(float* p, long i, float v) { p[i] = v; }
+template <> __device__ __forceinline__ void st<__nv_bfloat16>(__nv_bfloat16* p, long i, float v) {
+    p[i] = __float2bfloat16_rn(v);
+}
+
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float x) {
+    return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
+}
+
+// ky index of retained row r: 0..M-1 then NY-M..NY-1
+__device__ __forceinline__ int ky_of(int r, int M, int NY) { return r < M ? r : NY - 2 * M + r; }
+
+// 1x1 channel map: Y[b][co][p] = sum_ci Wt[co][ci] X[b][ci][p] + bias[co] (times scale)
+template <typename SI, typename SO>
+__global__ void k_chan(const SI* __restrict__ X, const float* __restrict__ Wt, const float* __restrict__ bias,
+                       SO* __restrict__ Y, int Ci, int Co, long P, int B, float scale, int transpose) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)B * P) return;
+    const int b = (int)(idx / P);
+    const long p = idx % P;
+    float x[32];
+    for (int ci = 0; ci < Ci; ++ci) x[ci] = ld(X, ((long)b * Ci + ci) * P + p);
+    for (int co = 0; co < Co; ++co) {
+        float acc = bias ? bias[co] : 0.f;
+        for (int ci = 0; ci < Ci; ++ci) acc += (transpose ? Wt[ci * Co + co] : Wt[co * Ci + ci]) * x[ci];
+        st(Y, ((long)b * Co + co) * P + p, acc * scale);
+    }
+}
+
+// A[row][kx] = sum_x X[row][x] e^{-2 pi i kx x / NX} * colscale(kx); rows = B W NY
+template <typename SI>
+__global__ void k_dft_x(const SI* __restrict__ X, float2* __restrict__ A, const float2* __restrict__ twx, long rows,
+                        int NX, int M, float scale0, float scale1) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * M) return;
+    const long row = idx / M;
+    const int kx = (int)(idx % M);
+    float re = 0.f, im = 0.f;
+    for (int x = 0; x < NX; ++x) {
+        const float v = ld(X, row * NX + x);
+        const float2 w = twx[kx * NX + x];
+        re += v * w.x;
+        im += v * w.y;
+    }
+    const float s = kx == 0 ? scale0 : scale1;
+    A[idx] = make_float2(re * s, im * s);
+}
+
+// along y between NY rows and the 2M retained rows; fwd: out[r] = sum_y in[y]
+// e^{sign 2 pi i ky(r) y / NY} (NY -> 2M); adjoint direction (2M -> NY):
+// out[y] = sum_r in[r] e^{sign 2 pi i ky(r) y / NY}
+__global__ void k_dft_y(const float2* __restrict__ in, float2* __restrict__ out, const float2* __restrict__ twy, int BW,
+                        int NY, int M, int to_modes, float sign) {
+    const int MY = 2 * M;
+    const long nout = (long)BW * (to_modes ? MY : NY) * M;
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nout) return;
+    const int kx = (int)(idx % M);
+    const long rest = idx / M;
+    const int nrow_out = to_modes ? MY : NY;
+    const int r = (int)(rest % nrow_out);
+    const long bw = rest / nrow_out;
+    float re = 0.f, im = 0.f;
+    const int nin = to_modes ? NY : MY;
+    for (int j = 0; j < nin; ++j) {
+        const int y = to_modes ? j : r;
+        const int mr = to_modes ? r : j;
+        float2 w = twy[mr * NY + y];             // e^{-2 pi i ky y / NY}
+        w.y *= -sign;                            // sign -1: as tabulated, +1: conjugate
+        const float2 v = in[(bw * nin + j) * M + kx];
+        re += v.x * w.x - v.y * w.y;
+        im += v.x * w.y + v.y * w.x;
+    }
+    out[idx] = make_float2(re, im);
+}
+
+// T[b][co][k] = sum_ci R[co][ci][k] S[b][ci][k]; adjoint: S' = sum_co conj(R[co][ci]) T
+__global__ void k_mix(const float2* __restrict__ in, const float2* __restrict__ R, float2* __restrict__ out, int B, int W,
+                      int K, int adjoint) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)B * W * K) return;
+    const int k = (int)(idx % K);
+    const int o = (int)((idx / K) % W);
+    const int b = (int)(idx / ((long)K * W));
+    float re = 0.f, im = 0.f;
+    for (int i = 0; i < W; ++i) {
+        float2 r = adjoint ? R[((long)i * W + o) * K + k] : R[((long)o * W + i) * K + k];
+        if (adjoint) r.y = -r.y;
+        const float2 v = in[((long)b * W + i) * K + k];
+        re += r.x * v.x - r.y * v.y;
+        im += r.x * v.y + r.y * v.x;
+    }
+    out[idx] = make_float2(re, im);
+}
+
+// dR[co][ci][k] += sum_b dT[b][co][k] conj(S[b][ci][k])
+__global__ void k_mix_grad(const float2* __restrict__ dT, const float2* __restrict__ S, float2* __restrict__ dR, int B,
+                           int W, int K) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)W * W * K) return;
+    const int k = (int)(idx % K);
+    const int ci = (int)((idx / K) % W);
+    const int co = (int)(idx / ((long)K * W));
+    float re = 0.f, im = 0.f;
+    for (int b = 0; b < B; ++b) {
+        const float2 g = dT[((long)b * W + co) * K + k];
+        const float2 s = S[((long)b * W + ci) * K + k];
+        re += g.x * s.x + g.y * s.y;
+        im += g.y * s.x - g.x * s.y;
+    }
+    dR[idx].x += re;
+    dR[idx].y += im;
+}
+
+// a[b][co][p] = W v + bias + IDFT_x(U)[co][y][x];  v_next = GELU(a) or a
+template <typename SS>
+__global__ void k_layer_out(const SS* __restrict__ v, const float2* __restrict__ U, const float* __restrict__ Wt,
+                            const float* __restrict__ bias, const float2* __restrict__ twx, SS* __restrict__ a_out,
+                            SS* __restrict__ v_next, int B, int W, int NY, int NX, int M, int last) {
+    const long P = (long)NY * NX;
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)B * P) return;
+    const int b = (int)(idx / P);
+    const long p = idx % P;
+    const int y = (int)(p / NX), x = (int)(p % NX);
+    float vin[32];
+    for (int ci = 0; ci < W; ++ci) vin[ci] = ld(v, ((long)b * W + ci) * P + p);
+    const float inv = 1.f / (float)P;
+    for (int co = 0; co < W; ++co) {
+        float acc = bias[co];
+        for (int ci = 0; ci < W; ++ci) acc += Wt[co * W + ci] * vin[ci];
+        const float2* u = U + (((long)b * W + co) * NY + y) * M;
+        float z = 0.f;
+        for (int kx = 0; kx < M; ++kx) {
+            const float2 w = twx[kx * NX + x];      // conj gives e^{+i theta}
+            const float re = u[kx].x * w.x + u[kx].y * w.y;
+            z += (kx == 0 ? 1.f : 2.f) * re;
+        }
+        acc += z * inv;
+        const long o = ((long)b * W + co) * P + p;
+        st(a_out, o, acc);
+        st(v_next, o, last ? acc : gelu(acc));
+    }
+}
+
+// da = dvn * GELU'(a) (or dvn for the last layer), FP32 in place
+template <typename SS>
+__global__ void k_gelu_bwd(float* __restrict__ dv, const SS* __restrict__ a, long n, int last) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || last) return;
+    dv[i] *= gelu_grad(ld(a, i));
+}
+
+// dX[row][x] (+)= Re(sum_kx dA[row][kx] e^{+2 pi i kx x / NX})
+__global__ void k_dft_x_adj(const float2* __restrict__ dA, float* __restrict__ dX, const float2* __restrict__ twx,
+                            long rows, int NX, int M, int accumulate) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * NX) return;
+    const long row = idx / NX;
+    const int x = (int)(idx % NX);
+    float s = 0.f;
+    for (int kx = 0; kx < M; ++kx) {
+        const float2 g = dA[row * M + kx];
+        const float2 w = twx[kx * NX + x];
+        s += g.x * w.x + g.y * w.y;             // Re(g conj(w))
+    }
+    dX[idx] = accumulate ? dX[idx] + s : s;
+}
+
+// dW[co][ci] += sum_{b,p} dY[b][co][p] X[b][ci][p]; db[co] += sum dY
+template <typename SX>
+__global__ void k_wgrad(const float* __restrict__ dY, const SX* __restrict__ X, float* __restrict__ dW,
+                        float* __restrict__ db, int Co, int Ci, long P, int B) {
+    const int co = blockIdx.y, ci = blockIdx.z;   // ci == Ci: bias
+    __shared__ float red[256];
+    float acc = 0.f;
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long)B * P; idx += (long)gridDim.x * blockDim.x) {
+        const int b = (int)(idx / P);
+        const long p = idx % P;
+        const float g = dY[((long)b * Co + co) * P + p];
+        acc += ci < Ci ? g * ld(X, ((long)b * Ci + ci) * P + p) : g;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(ci < Ci ? &dW[co * Ci + ci] : &db[co], red[0]);
+}
+
+// per-sample sums of (h - t)^2 and t^2
+__global__ void k_loss_sums(const float* __restrict__ h, const float* __restrict__ t, double* __restrict__ red, long n) {
+    const int b = blockIdx.y;
+    __shared__ double r1[256], r2[256];
+    double s1 = 0, s2 = 0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const double d = (double)h[b * n + i] - t[b * n + i];
+        s1 += d * d;
+        s2 += (double)t[b * n + i] * t[b * n + i];
+    }
+    r1[threadIdx.x] = s1;
+    r2[threadIdx.x] = s2;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if (threadIdx.x < k) {
+            r1[threadIdx.x] += r1[threadIdx.x + k];
+            r2[threadIdx.x] += r2[threadIdx.x + k];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(&red[2 * b], r1[0]);
+        atomicAdd(&red[2 * b + 1], r2[0]);
+    }
+}
+
+// dh = 2 (h - t) / (B sum t^2)
+__global__ void k_loss_grad(const float* __restrict__ h, const float* __restrict__ t, const double* __restrict__ red,
+                            float* __restrict__ dh, long n, int B) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long)B * n) return;
+    const int b = (int)(i / n);
+    dh[i] = (float)(2.0 * ((double)h[i] - t[i]) / (B * red[2 * b + 1]));
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void k_init_tw(float2* twx, float2* twy, int NX, int NY, int M) {
+    const int total = M * NX + 2 * M * NY;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        double s, c;
+        if (i < M * NX) {
+            const int kx = i / NX, x = i % NX;
+            sincospi(-2.0 * (double)((long)kx * x % NX) / NX, &s, &c);
+            twx[i] = make_float2((float)c, (float)s);
+        } else {
+            const int j = i - M * NX;
+            const int r = j / NY, y = j % NY;
+            const int ky = ky_of(r, M, NY);
+            sincospi(-2.0 * (double)((long)ky * y % NY) / NY, &s, &c);
+            twy[j] = make_float2((float)c, (float)s);
+        }
+    }
+}
+
+constexpr int kFT = 256;
+inline unsigned g1(long n) { return (unsigned)((n + kFT - 1) / kFT); }
+
+int ffail(mm_fno* f, int code, const char* msg) {
+    if (f) f->err = msg;
+    return fail(nullptr, code, "%s", msg);
+}
+
+#define FNO_CHECK(f)                                                                           \
+    do {                                                                                       \
+        cudaError_t e_ = cudaGetLastError();                                                   \
+        if (e_ != cudaSuccess) return ffail((f), MM_ERR_CUDA, cudaGetErrorString(e_));         \
+    } while (0)
+
+template <typename SS> int forward_t(mm_fno* f, const float* m, float* h, int B) {
+    const long P = f->P;
+    const int W = f->W, NX = f->nx, NY = f->ny, M = f->M, K = f->K;
+    SS* v = (SS*)f->v;
+    SS* a = (SS*)f->a;
+    const long vs = (long)f->max_batch * W * P;
+    k_chan<float, SS><<<g1((long)B * P), kFT, 0, f->stream>>>(m, f->params + f->o_P, f->params + f->o_p, v, 3, W, P, B,
+                                                              1.f, 0);
+    FNO_CHECK(f);
+    for (int l = 0; l < f->L; ++l) {
+        SS* vl = v + l * vs;
+        float2* S = f->S + (long)l * f->max_batch * W * K;
+        k_dft_x<SS><<<g1((long)B * W * NY * M), kFT, 0, f->stream>>>(vl, f->A, f->twx, (long)B * W * NY, NX, M, 1.f, 1.f);
+        k_dft_y<<<g1((long)B * W * 2 * M * M), kFT, 0, f->stream>>>(f->A, S, f->twy, B * W, NY, M, 1, -1.f);
+        k_mix<<<g1((long)B * W * K), kFT, 0, f->stream>>>(S, (const float2*)(f->params + f->o_R[l]), f->T, B, W, K, 0);
+        k_dft_y<<<g1((long)B * W * NY * M), kFT, 0, f->stream>>>(f->T, f->U, f->twy, B * W, NY, M, 0, 1.f);
+        k_layer_out<SS><<<g1((long)B * P), kFT, 0, f->stream>>>(vl, f->U, f->params + f->o_W[l], f->params + f->o_b[l],
+                                                                f->twx, a + l * vs, v + (l + 1) * vs, B, W, NY, NX, M,
+                                                                l == f->L - 1);
+        FNO_CHECK(f);
+    }
+    k_chan<SS, float><<<g1((long)B * P), kFT, 0, f->stream>>>(v + f->L * vs, f->params + f->o_Q, f->params + f->o_q, h, W,
+                                                              3, P, B, f->out_scale, 0);
+    FNO_CHECK(f);
+    return MM_OK;
+}
+
+template <typename SS> int backward_t(mm_fno* f, const float* dh, int B) {
+    const long P = f->P;
+    const int W = f->W, NX = f->nx, NY = f->ny, M = f->M, K = f->K;
+    SS* v = (SS*)f->v;
+    SS* a = (SS*)f->a;
+    const long vs = (long)f->max_batch * W * P;
+    float* dv = (float*)f->dv;
+    float* dv2 = dv + vs;
+    float* G = f->grads;
+    // projection: dQ += dh v_L^T, dq += sum dh, dv_L = Q^T dh
+    dim3 gq(64, 3, W + 1);
+    k_wgrad<SS><<<gq, 256, 0, f->stream>>>(dh, v + f->L * vs, G + f->o_Q, G + f->o_q, 3, W, P, B);
+    k_chan<float, float><<<g1((long)B * P), kFT, 0, f->stream>>>(dh, f->params + f->o_Q, nullptr, dv, 3, W, P, B, 1.f, 1);
+    FNO_CHECK(f);
+    for (int l = f->L - 1; l >= 0; --l) {
+        SS* vl = v + l * vs;
+        float2* S = f->S + (long)l * f->max_batch * W * K;
+        // da = dv * GELU'(a)
+        k_gelu_bwd<SS><<<g1((long)B * W * P), kFT, 0, f->stream>>>(dv, a + l * vs, (long)B * W * P, l == f->L - 1);
+        // channel part
+        dim3 gw(64, W, W + 1);
+        k_wgrad<SS><<<gw, 256, 0, f->stream>>>(dv, vl, G + f->o_W[l], G + f->o_b[l], W, W, P, B);
+        k_chan<float, float><<<g1((long)B * P), kFT, 0, f->stream>>>(dv, f->params + f->o_W[l], nullptr, dv2, W, W, P, B,
+                                                                     1.f, 1);
+        // spectral part: dU = c / P sum_x da e^{-i theta}
+        k_dft_x<float><<<g1((long)B * W * NY * M), kFT, 0, f->stream>>>(dv, f->U, f->twx, (long)B * W * NY, NX, M,
+                                                                       1.f / (float)P, 2.f / (float)P);
+        k_dft_y<<<g1((long)B * W * 2 * M * M), kFT, 0, f->stream>>>(f->U, f->T, f->twy, B * W, NY, M, 1, -1.f);
+        k_mix_grad<<<g1((long)W * W * K), kFT, 0, f->stream>>>(f->T, S, (float2*)(G + f->o_R[l]), B, W, K);
+        // dS = R^H dT into U (free again; the stored spectra S stay intact for a later backward)
+        k_mix<<<g1((long)B * W * K), kFT, 0, f->stream>>>(f->T, (const float2*)(f->params + f->o_R[l]), f->U, B, W, K, 1);
+        k_dft_y<<<g1((long)B * W * NY * M), kFT, 0, f->stream>>>(f->U, f->A, f->twy, B * W, NY, M, 0, 1.f);
+        k_dft_x_adj<<<g1((long)B * W * NY * NX), kFT, 0, f->stream>>>(f->A, dv2, f->twx, (long)B * W * NY, NX, M, 1);
+        FNO_CHECK(f);
+        std::swap(dv, dv2);
+    }
+    return MM_OK;
+}
+
+}  // namespace
+
+void fno_grid(const mm_fno* f, int* nx, int* ny) {
+    *nx = f->nx;
+    *ny = f->ny;
+}
+
+cudaStream_t fno_swap_stream(mm_fno* f, cudaStream_t s) {
+    cudaStream_t old = f->stream;
+    f->stream = s;
+    return old;
+}
+
+}  // namespace mm
+
+using namespace mm;
+
+extern "C" {
+
+int mm_fno_create(mm_fno** out, int nx, int ny, int width, int modes, int layers, int store_bf16, int max_batch,
+                  unsigned long long seed, void* stream) {
+    if (!out) return fail(nullptr, MM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (nx < 2 || ny < 2 || width < 1 || width > 32 || modes < 1 || 2 * modes > ny || modes > nx / 2 || layers < 1 ||
+        max_batch < 1)
+        return fail(nullptr, MM_ERR_INVALID_ARG, "FNO sizes: width <= 32, 2 modes <= ny, modes <= nx / 2");
+    mm_fno* f = new mm_fno();
+    f->nx = nx;
+    f->ny = ny;
+    f->W = width;
+    f->M = modes;
+    f->L = layers;
+    f->store_bf16 = store_bf16 ? 1 : 0;
+    f->max_batch = max_batch;
+    f->stream = (cudaStream_t)stream;
+    f->P = (long)nx * ny;
+    f->MY = 2 * modes;
+    f->K = f->MY * modes;
+    f->out_scale = 1.f;
+    int dev = 0;
+    cudaError_t ce = stream ? cudaStreamGetDevice(f->stream, &dev) : cudaGetDevice(&dev);
+    if (ce == cudaSuccess) ce = cudaSetDevice(dev);
+    f->device = dev;
+    // parameter layout
+    long o = 0;
+    f->o_P = o; o += 3L * width;
+    f->o_p = o; o += width;
+    for (int l = 0; l < layers; ++l) {
+        f->o_W.push_back(o); o += (long)width * width;
+        f->o_b.push_back(o); o += width;
+        f->o_R.push_back(o); o += 2L * width * width * f->K;
+    }
+    f->o_Q = o; o += 3L * width;
+    f->o_q = o; o += 3;
+    f->nparams = o;
+    const size_t es = f->store_bf16 ? 2 : 4;
+    const long vs = (long)max_batch * width * f->P;
+    bool ok = ce == cudaSuccess;
+    auto A = [&](void** p, size_t bytes) {
+        if (ok && cudaMalloc(p, bytes) != cudaSuccess) ok = false;
+    };
+    A((void**)&f->params, o * 4);
+    A((void**)&f->grads, o * 4);
+    A((void**)&f->adam_m, o * 4);
+    A((void**)&f->adam_v, o * 4);
+    A(&f->v, (size_t)(layers + 1) * vs * es);
+    A(&f->a, (size_t)layers * vs * es);
+    A((void**)&f->S, (size_t)layers * max_batch * width * f->K * sizeof(float2));
+    A((void**)&f->A, (size_t)max_batch * width * ny * modes * sizeof(float2));
+    A((void**)&f->T, (size_t)max_batch * width * f->K * sizeof(float2));
+    A((void**)&f->U, (size_t)max_batch * width * ny * modes * sizeof(float2));
+    A(&f->dv, 2 * (size_t)vs * 4);
+    A((void**)&f->twx, (size_t)modes * nx * sizeof(float2));
+    A((void**)&f->twy, (size_t)2 * modes * ny * sizeof(float2));
+    A((void**)&f->red, (size_t)2 * max_batch * sizeof(double));
+    if (!ok) {
+        cudaGetLastError();
+        mm_fno_destroy(f);
+        return fail(nullptr, MM_ERR_NOMEM, "FNO allocation failed");
+    }
+    // initialisation: uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) for 1x1 maps,
+    // spectral weights uniform * 1/(W W), biases 0 (seeded host generator)
+    std::vector<float> h(o, 0.f);
+    unsigned long long s = seed * 6364136223846793005ull + 1442695040888963407ull;
+    auto rnd = [&]() {
+        s = s * 6364136223846793005ull + 1442695040888963407ull;
+        return ((double)(s >> 11) / 9007199254740992.0) * 2.0 - 1.0;
+    };
+    for (long i = 0; i < 3L * width; ++i) h[f->o_P + i] = (float)(rnd() / std::sqrt(3.0));
+    for (int l = 0; l < layers; ++l) {
+        for (long i = 0; i < (long)width * width; ++i) h[f->o_W[l] + i] = (float)(rnd() / std::sqrt((double)width));
+        for (long i = 0; i < 2L * width * width * f->K; ++i) h[f->o_R[l] + i] = (float)(rnd() / ((double)width * width));
+    }
+    for (long i = 0; i < 3L * width; ++i) h[f->o_Q + i] = (float)(rnd() / std::sqrt((double)width));
+    ce = cudaMemcpy(f->params, h.data(), o * 4, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemset(f->grads, 0, o * 4);
+    if (ce == cudaSuccess) ce = cudaMemset(f->adam_m, 0, o * 4);
+    if (ce == cudaSuccess) ce = cudaMemset(f->adam_v, 0, o * 4);
+    k_init_tw<<<64, 256, 0, f->stream>>>(f->twx, f->twy, nx, ny, modes);
+    if (ce == cudaSuccess) ce = cudaGetLastError();
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(f->stream);
+    if (ce != cudaSuccess) {
+        mm_fno_destroy(f);
+        return fail(nullptr, MM_ERR_CUDA, "FNO setup: %s", cudaGetErrorString(ce));
+    }
+    *out = f;
+    return MM_OK;
+}
+
+void mm_fno_destroy(mm_fno* f) {
+    if (!f) return;
+    cudaSetDevice(f->device);
+    cudaStreamSynchronize(f->stream);
+    void* ptrs[] = {f->params, f->grads, f->adam_m, f->adam_v, f->v, f->a, f->S, f->A, f->T, f->U, f->dv, f->twx, f->twy, f->red};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete f;
+}
+
+long mm_fno_num_params(const mm_fno* f) { return f ? f->nparams : 0; }
+
+int mm_fno_forward(mm_fno* f, const void* m, void* h, int batch) {
+    if (!f || !m || !h || batch < 1 || batch > f->max_batch) return fail(nullptr, MM_ERR_INVALID_ARG, "mm_fno_forward: bad arguments");
+    if (cudaSetDevice(f->device) != cudaSuccess) return fail(nullptr, MM_ERR_CUDA, "cudaSetDevice");
+    return f->store_bf16 ? forward_t<__nv_bfloat16>(f, (const float*)m, (float*)h, batch)
+                         : forward_t<float>(f, (const float*)m, (float*)h, batch);
+}
+
+int mm_fno_backward(mm_fno* f, const void* m, const void* dh, int batch) {
+    if (!f || !m || !dh || batch < 1 || batch > f->max_batch) return fail(nullptr, MM_ERR_INVALID_ARG, "mm_fno_backward: bad arguments");
+    if (f->out_scale != 1.f) return ffail(f, MM_ERR_INVALID_ARG, "mm_fno_backward: output scale must be 1 while training");
+    if (cudaSetDevice(f->device) != cudaSuccess) return fail(nullptr, MM_ERR_CUDA, "cudaSetDevice");
+    int rc = f->store_bf16 ? backward_t<__nv_bfloat16>(f, (const float*)dh, batch) : backward_t<float>(f, (const float*)dh, batch);
+    if (rc) return rc;
+    // lift: dP += dv_0 m^T, dp += sum dv_0 (dv_0 ends in the buffer the last swap selected)
+    const long vs = (long)f->max_batch * f->W * f->P;
+    float* dv0 = (float*)f->dv + ((f->L % 2) ? vs : 0);
+    dim3 gp(64, f->W, 4);
+    k_wgrad<float><<<gp, 256, 0, f->stream>>>(dv0, (const float*)m, f->grads + f->o_P, f->grads + f->o_p, f->W, 3, f->P, batch);
+    FNO_CHECK(f);
+    return MM_OK;
+}
+
+int mm_fno_zero_grad(mm_fno* f) {
+    if (!f) return fail(nullptr, MM_ERR_INVALID_ARG, "fno is NULL");
+    cudaSetDevice(f->device);
+    cudaError_t e = cudaMemsetAsync(f->grads, 0, f->nparams * 4, f->stream);
+    return e == cudaSuccess ? MM_OK : ffail(f, MM_ERR_CUDA, cudaGetErrorString(e));
+}
+
+int mm_fno_adam_step(mm_fno* f, double lr, double beta1, double beta2, double eps, long step) {
+    if (!f || step < 1) return fail(nullptr, MM_ERR_INVALID_ARG, "mm_fno_adam_step: bad arguments");
+    cudaSetDevice(f->device);
+    const float c1 = (float)(1.0 - std::pow(beta1, (double)step)), c2 = (float)(1.0 - std::pow(beta2, (double)step));
+    k_adam<<<g1(f->nparams), kFT, 0, f->stream>>>(f->params, f->grads, f->adam_m, f->adam_v, f->nparams, (float)lr,
+                                                  (float)beta1, (float)beta2, (float)eps, c1, c2);
+    FNO_CHECK(f);
+    return MM_OK;
+}
+
+int mm_fno_loss(mm_fno* f, const void* h, const void* target, void* dh, int batch, double* loss_out) {
+    if (!f || !h || !target || batch < 1 || batch > f->max_batch) return fail(nullptr, MM_ERR_INVALID_ARG, "mm_fno_loss: bad arguments");
+    cudaSetDevice(f->device);
+    const long n = 3 * f->P;
+    cudaError_t e = cudaMemsetAsync(f->red, 0, 2 * batch * sizeof(double), f->stream);
+    if (e != cudaSuccess) return ffail(f, MM_ERR_CUDA, cudaGetErrorString(e));
+    dim3 g(64, batch);
+    k_loss_sums<<<g, 256, 0, f->stream>>>((const float*)h, (const float*)target, f->red, n);
+    if (dh) k_loss_grad<<<g1(batch * n), kFT, 0, f->stream>>>((const float*)h, (const float*)target, f->red, (float*)dh, n, batch);
+    FNO_CHECK(f);
+    if (loss_out) {
+        std::vector<double> r(2 * batch);
+        e = cudaMemcpyAsync(r.data(), f->red, 2 * batch * sizeof(double), cudaMemcpyDeviceToHost, f->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
+        if (e != cudaSuccess) return ffail(f, MM_ERR_CUDA, cudaGetErrorString(e));
+        double L = 0;
+        for (int b = 0; b < batch; ++b) L += r[2 * b] / r[2 * b + 1];
+        *loss_out = L / batch;
+    }
+    return MM_OK;
+}
+
+int mm_fno_params(mm_fno* f, float* host_params, float* host_grads, const float* host_set) {
+    if (!f) return fail(nullptr, MM_ERR_INVALID_ARG, "fno is NULL");
+    cudaSetDevice(f->device);
+    cudaError_t e = cudaStreamSynchronize(f->stream);
+    if (e == cudaSuccess && host_set) e = cudaMemcpy(f->params, host_set, f->nparams * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && host_params) e = cudaMemcpy(host_params, f->params, f->nparams * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && host_grads) e = cudaMemcpy(host_grads, f->grads, f->nparams * 4, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? MM_OK : ffail(f, MM_ERR_CUDA, cudaGetErrorString(e));
+}
+
+int mm_fno_set_output_scale(mm_fno* f, double scale) {
+    if (!f) return fail(nullptr, MM_ERR_INVALID_ARG, "fno is NULL");
+    f->out_scale = (float)scale;
+    return MM_OK;
+}
+
+}  // extern "C"

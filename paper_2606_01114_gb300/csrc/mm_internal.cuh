@@ -171,6 +171,9 @@ int tc_prepare(mm_ctx* ctx);
 int demag_setup(mm_ctx* ctx);                          // K1: Newell tensor -> k-space octant
 int demag_apply(mm_ctx* ctx, const void* m, void* H);  // K2..K6
 int demag_apply_unit(mm_ctx* ctx, const void* g, void* H);  // same with Ms = 1 (adjoint)
+// surrogate network: its grid, and the stream its launches go to (returns the old one)
+void fno_grid(const mm_fno* f, int* nx, int* ny);
+cudaStream_t fno_swap_stream(mm_fno* f, cudaStream_t s);
 
 // ----- Newell (mm_newell.cu)
 // Fills the FP64 real-space padded grid [Pz][Py][Px] of component c (0..5)

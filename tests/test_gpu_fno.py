@@ -1,0 +1,222 @@
+"""The FNO demag surrogate's GPU kernels through the C ABI: forward outputs
+and parameter gradients against the float64 oracle network (same
+parameters, same inputs), FP32 and BF16 activation storage; a short Adam run
+on exact thin-film demag fields lowers the loss; relax() with the surrogate
+falls back to the exact field when the residual is above the bound and uses
+the surrogate when it is within it."""
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import fno as ofno
+
+torch = pytest.importorskip("torch")
+import paper_2606_01114_gb300 as mm  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2606_01114_gb300 import build
+    build.build()
+
+
+def n_params(W, M, L):
+    return 3 * W + W + L * (W * W + W + 2 * W * W * 2 * M * M) + 3 * W + 3
+
+
+def random_params(W, M, L, seed):
+    rng = np.random.default_rng(seed)
+    parts = [rng.standard_normal(3 * W) / np.sqrt(3), rng.standard_normal(W) * 0.1]
+    for _ in range(L):
+        parts += [rng.standard_normal(W * W) / np.sqrt(W), rng.standard_normal(W) * 0.1,
+                  rng.standard_normal(2 * W * W * 2 * M * M) / (W * 4)]
+    parts += [rng.standard_normal(3 * W) / np.sqrt(W), rng.standard_normal(3) * 0.1]
+    p = np.concatenate(parts).astype(np.float32)
+    assert p.size == n_params(W, M, L)
+    return p
+
+
+def blocks(W, M, L):
+    names = [("P", 3 * W), ("p", W)]
+    for l in range(L):
+        names += [(f"W{l}", W * W), (f"b{l}", W), (f"R{l}", 2 * W * W * 2 * M * M)]
+    names += [("Q", 3 * W), ("q", 3)]
+    o = 0
+    for name, n in names:
+        yield name, slice(o, o + n)
+        o += n
+
+
+def sample_m(B, NY, NX, seed):
+    ms = [wl.random_unit((NX, NY, 1), seed=seed + b)[:, 0] for b in range(B)]
+    ms[0] = wl.vortex((NX, NY, 1), (4e-9, 4e-9, 4e-9))[:, 0]
+    return np.stack(ms).astype(np.float32)
+
+
+CASES = [  # (NY, NX, W, M, L, B)
+    (32, 32, 8, 4, 3, 2),
+    (24, 40, 5, 6, 2, 3),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("bf16", [False, True])
+def test_forward_and_gradients_match_oracle(case, bf16):
+    NY, NX, W, M, L, B = case
+    f = mm.mm_fno_create(NX, NY, width=W, modes=M, layers=L, store_bf16=bf16, max_batch=4, seed=1)
+    assert mm.mm_fno_num_params(f) == n_params(W, M, L)
+    params = random_params(W, M, L, seed=2)
+    mm.mm_fno_params(f, set_params=params)
+    m = sample_m(B, NY, NX, seed=3)
+    target = np.random.default_rng(4).standard_normal(m.shape).astype(np.float32)
+    md, td = torch.tensor(m, device="cuda"), torch.tensor(target, device="cuda")
+    h = torch.empty_like(md)
+    mm.mm_fno_forward(f, md, h)
+    h_ref = ofno.forward(params.astype(np.float64), m, W, M, L).numpy()
+    err = np.linalg.norm(h.cpu().numpy() - h_ref) / np.linalg.norm(h_ref)
+    assert err < (2e-2 if bf16 else 2e-5), err
+
+    dh = torch.empty_like(md)
+    loss = mm.mm_fno_loss(f, h, td, dh)
+    mm.mm_fno_zero_grad(f)
+    mm.mm_fno_backward(f, md, dh)
+    _, g = mm.mm_fno_params(f)
+    L_ref, g_ref = ofno.loss_and_grad(params.astype(np.float64), m, target, W, M, L)
+    assert loss == pytest.approx(L_ref, rel=2e-2 if bf16 else 1e-5)
+    for name, sl in blocks(W, M, L):
+        e = np.linalg.norm(g[sl] - g_ref[sl]) / np.linalg.norm(g_ref[sl])
+        assert e < (5e-2 if bf16 else 1e-4), (name, e)
+    mm.mm_fno_destroy(f)
+
+
+def test_gradients_accumulate_and_zero():
+    NY, NX, W, M, L, B = CASES[0]
+    f = mm.mm_fno_create(NX, NY, width=W, modes=M, layers=L, store_bf16=False, max_batch=4, seed=1)
+    m = torch.tensor(sample_m(B, NY, NX, seed=5), device="cuda")
+    h, dh = torch.empty_like(m), torch.empty_like(m)
+    mm.mm_fno_forward(f, m, h)
+    mm.mm_fno_loss(f, h, m, dh)
+    mm.mm_fno_zero_grad(f)
+    mm.mm_fno_backward(f, m, dh)
+    g1 = mm.mm_fno_params(f)[1].copy()
+    mm.mm_fno_backward(f, m, dh)
+    g2 = mm.mm_fno_params(f)[1]
+    np.testing.assert_allclose(g2, 2 * g1, rtol=1e-5, atol=1e-7 * np.abs(g1).max())
+    mm.mm_fno_zero_grad(f)
+    assert not mm.mm_fno_params(f)[1].any()
+    mm.mm_fno_destroy(f)
+
+
+def test_invalid_sizes_and_training_with_output_scale_rejected():
+    with pytest.raises(mm.MMError):
+        mm.mm_fno_create(32, 32, width=33, modes=4, layers=2)
+    with pytest.raises(mm.MMError):
+        mm.mm_fno_create(32, 32, width=8, modes=17, layers=2)
+    with pytest.raises(mm.MMError):
+        mm.mm_fno_create(32, 8, width=8, modes=5, layers=2)
+    f = mm.mm_fno_create(16, 16, width=4, modes=2, layers=1, max_batch=2)
+    m = torch.zeros((3, 3, 16, 16), device="cuda")
+    with pytest.raises(mm.MMError):
+        mm.mm_fno_forward(f, m, torch.empty_like(m))       # batch 3 > max_batch 2
+    m = torch.zeros((1, 3, 16, 16), device="cuda")
+    mm.mm_fno_set_output_scale(f, 8e5)
+    with pytest.raises(mm.MMError):
+        mm.mm_fno_backward(f, m, m)
+    mm.mm_fno_destroy(f)
+
+
+FILM = dict(n=(64, 64, 1), d=(4e-9, 4e-9, 4e-9), Ms=8e5, A=1.3e-11)
+
+
+def film_ctx():
+    ctx = mm.mm_init_mesh(*FILM["n"], *FILM["d"], precision=mm.MM_F32)
+    mm.mm_set_material(ctx, FILM["Ms"], FILM["A"], 0.5, 0.0, (0, 0, 1))
+    return ctx
+
+
+def training_pairs(ctx, count, seed):
+    ms, hs = [], []
+    for i in range(count):
+        m = wl.film_state(FILM["n"], FILM["d"], seed=seed + i)
+        md = torch.tensor(m, dtype=torch.float32, device="cuda")
+        H = torch.empty_like(md)
+        mm.mm_demag_field(ctx, md, H)
+        ms.append(md[:, 0])
+        hs.append(H[:, 0] / FILM["Ms"])
+    return torch.stack(ms).contiguous(), torch.stack(hs).contiguous()
+
+
+def train(f, ms, hs, steps, batch, lr):
+    losses = []
+    for s in range(1, steps + 1):
+        i = ((s - 1) * batch) % ms.shape[0]
+        mb, hb = ms[i:i + batch].contiguous(), hs[i:i + batch].contiguous()
+        out, dh = torch.empty_like(mb), torch.empty_like(mb)
+        mm.mm_fno_forward(f, mb, out)
+        losses.append(mm.mm_fno_loss(f, out, hb, dh))
+        mm.mm_fno_zero_grad(f)
+        mm.mm_fno_backward(f, mb, dh)
+        mm.mm_fno_adam_step(f, lr, step=s)
+    return losses
+
+
+def test_adam_training_lowers_the_loss_on_exact_demag_fields():
+    ctx = film_ctx()
+    ms, hs = training_pairs(ctx, 24, seed=10)
+    f = mm.mm_fno_create(64, 64, width=16, modes=8, layers=3, store_bf16=True, max_batch=8, seed=3)
+    losses = train(f, ms, hs, steps=150, batch=8, lr=3e-3)
+    assert np.all(np.isfinite(losses))
+    first, last = np.mean(losses[:3]), np.mean(losses[-3:])
+    assert last < 0.2 * first, (first, last)
+    mm.mm_fno_destroy(f)
+    mm.mm_destroy(ctx)
+
+
+def test_relax_falls_back_to_exact_field_above_the_bound():
+    ctx = film_ctx()
+    f = mm.mm_fno_create(64, 64, width=8, modes=4, layers=2, max_batch=1, seed=4)   # untrained
+    m0 = torch.tensor(wl.vortex(FILM["n"], FILM["d"]), dtype=torch.float32, device="cuda")
+    m = m0.clone()
+    t, steps, exact, sur, fb = mm.mm_relax_surrogate(ctx, f, m, 5e-9, torque_tol=1e-2, k_exact=10, bound=1e-3)
+    # every window fell back (the last window start met the torque and ran no
+    # steps): one surrogate evaluation per window start and six exact stage
+    # fields per RKF45 trial besides the window starts' own
+    assert fb == sur - 1 and sur >= 2
+    assert (exact - sur) % 6 == 0 and exact - sur >= 6 * steps
+    m_ref = m0.clone()
+    mm.mm_relax(ctx, m_ref, 5e-9, 1e-2)
+    E, E_ref = mm.mm_energy(ctx, m), mm.mm_energy(ctx, m_ref)
+    assert sum(E) == pytest.approx(sum(E_ref), rel=1e-3)
+    assert mm.mm_max_torque(ctx, m) <= 1e-2
+    mm.mm_fno_destroy(f)
+    mm.mm_destroy(ctx)
+
+
+def test_relax_uses_the_surrogate_within_the_bound():
+    ctx = film_ctx()
+    f = mm.mm_fno_create(64, 64, width=8, modes=4, layers=2, max_batch=1, seed=4)
+    m = torch.tensor(wl.vortex(FILM["n"], FILM["d"]), dtype=torch.float32, device="cuda")
+    t, steps, exact, sur, fb = mm.mm_relax_surrogate(ctx, f, m, 2e-12, torque_tol=0.0, k_exact=5, bound=1e30)
+    assert fb == 0 and steps > 0 and t >= 2e-12
+    windows = exact
+    assert sur >= windows + 6 * steps
+    norm = torch.linalg.vector_norm(m, dim=0)
+    assert torch.all(torch.isfinite(m)) and float((norm - 1).abs().max()) < 1e-5
+    mm.mm_fno_destroy(f)
+    mm.mm_destroy(ctx)
+
+
+def test_relax_rejects_wrong_mesh():
+    f = mm.mm_fno_create(32, 32, width=4, modes=2, layers=1, max_batch=1)
+    for n, prec in (((64, 64, 1), mm.MM_F32), ((32, 32, 2), mm.MM_F32), ((32, 32, 1), mm.MM_F64)):
+        ctx = mm.mm_init_mesh(*n, 4e-9, 4e-9, 4e-9, precision=prec)
+        mm.mm_set_material(ctx, 8e5, 1.3e-11, 0.5, 0.0, (0, 0, 1))
+        m = torch.zeros(ctx.shape3, dtype=torch.float32 if prec == mm.MM_F32 else torch.float64, device="cuda")
+        m[2] = 1
+        with pytest.raises(mm.MMError):
+            mm.mm_relax_surrogate(ctx, f, m, 1e-12)
+        mm.mm_destroy(ctx)
+    mm.mm_fno_destroy(f)

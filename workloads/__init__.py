@@ -43,12 +43,13 @@ def uniform(n, direction=(0.0, 0.0, 1.0)):
     return np.broadcast_to(v[:, None, None, None], (3, nz, ny, nx)).copy()
 
 
-def vortex(n, d, core_radius=10e-9, noise=0.05, seed=1, chirality=1.0, polarity=1.0):
-    """Vortex centred on the mesh: m_z = p exp(-r^2 / rc^2), in-plane
-    c (-sin phi, cos phi) sqrt(1 - m_z^2), plus ``noise`` N(0, I3), renormalised."""
+def vortex(n, d, core_radius=10e-9, noise=0.05, seed=1, chirality=1.0, polarity=1.0, center=(0.0, 0.0)):
+    """Vortex at ``center`` (m, from the mesh centre): m_z = p exp(-r^2 / rc^2),
+    in-plane c (-sin phi, cos phi) sqrt(1 - m_z^2), plus ``noise`` N(0, I3),
+    renormalised."""
     nx, ny, nz = n
-    x = (np.arange(nx) + 0.5) * d[0] - nx * d[0] / 2
-    y = (np.arange(ny) + 0.5) * d[1] - ny * d[1] / 2
+    x = (np.arange(nx) + 0.5) * d[0] - nx * d[0] / 2 - center[0]
+    y = (np.arange(ny) + 0.5) * d[1] - ny * d[1] / 2 - center[1]
     Y, X = np.meshgrid(y, x, indexing="ij")
     r2 = X * X + Y * Y
     phi = np.arctan2(Y, X)
@@ -62,11 +63,12 @@ def vortex(n, d, core_radius=10e-9, noise=0.05, seed=1, chirality=1.0, polarity=
     return _unit(m)
 
 
-def domain_wall(n, d, width=20e-9, axis=0, seed=None, noise=0.0):
-    """Neel-type wall across the middle of ``axis``: m_z = -tanh(s / w)."""
+def domain_wall(n, d, width=20e-9, axis=0, seed=None, noise=0.0, offset=0.0):
+    """Neel-type wall across ``axis`` at ``offset`` (m) from the middle:
+    m_z = -tanh(s / w)."""
     nx, ny, nz = n
     coords = [(np.arange(k) + 0.5) * h - k * h / 2 for k, h in zip(n, d)]
-    s = coords[axis]
+    s = coords[axis] - offset
     mz = -np.tanh(s / width)
     mt = np.sqrt(1 - mz * mz)
     shape = [1, 1, 1]
@@ -96,3 +98,36 @@ def smooth_field(n, lo, hi, sigma_cells=8.0, seed=3):
     s = np.real(np.fft.ifftn(np.fft.fftn(w) * g))
     s = (s - s.min()) / (s.max() - s.min())
     return lo + (hi - lo) * s
+
+
+def smooth_unit(n, sigma_cells=4.0, seed=0):
+    """Unit vectors from three Gaussian-filtered N(0, 1) fields (periodic),
+    normalised: a random texture with correlation length ~sigma cells."""
+    nx, ny, nz = n
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal((3, nz, ny, nx))
+    k = [np.fft.fftfreq(m) for m in (nz, ny, nx)]
+    KZ, KY, KX = np.meshgrid(*k, indexing="ij")
+    g = np.exp(-2 * (np.pi * sigma_cells) ** 2 * (KX ** 2 + KY ** 2 + KZ ** 2))
+    v = np.real(np.fft.ifftn(np.fft.fftn(v, axes=(1, 2, 3)) * g, axes=(1, 2, 3)))
+    return _unit(v)
+
+
+def film_state(n, d, seed):
+    """One of four film textures, chosen and shaped by ``seed``: random unit
+    vectors, a vortex (random centre, chirality, polarity, core), a domain
+    wall (random axis, position, width) or a smooth random texture."""
+    rng = np.random.default_rng(seed)
+    kind = seed % 4
+    Lx, Ly = n[0] * d[0], n[1] * d[1]
+    if kind == 0:
+        return random_unit(n, seed=seed)
+    if kind == 1:
+        return vortex(n, d, core_radius=rng.uniform(5e-9, 20e-9), noise=rng.uniform(0.0, 0.2), seed=seed,
+                      chirality=rng.choice([-1.0, 1.0]), polarity=rng.choice([-1.0, 1.0]),
+                      center=(rng.uniform(-0.25, 0.25) * Lx, rng.uniform(-0.25, 0.25) * Ly))
+    if kind == 2:
+        axis = int(rng.integers(0, 2))
+        return domain_wall(n, d, width=rng.uniform(5e-9, 30e-9), axis=axis, seed=seed, noise=rng.uniform(0.0, 0.2),
+                           offset=rng.uniform(-0.3, 0.3) * (Lx if axis == 0 else Ly))
+    return smooth_unit(n, sigma_cells=rng.uniform(2.0, 12.0), seed=seed)
