@@ -268,15 +268,21 @@ int mm_fno_params(mm_fno* f, float* host_params, float* host_grads, const float*
 int mm_fno_set_output_scale(mm_fno* f, double scale);
 
 /* relax() with the surrogate: every k_exact accepted-step window starts
- * with the exact demag field of the current state, the surrogate's field of
- * the same state and their relative L2 residual; if the residual is at most
- * `bound` the window's RKF45 stages take their demag field from the
- * surrogate, else from the exact FFT convolution (a fallback).  Stops like
- * mm_relax (torque from the exact field at window starts).  MM_F32 context,
- * nz = 1, uniform Ms, surrogate of the same grid.  stats (nullable, 3
- * longs): exact demag evaluations, surrogate evaluations, fallbacks. */
+ * with the exact demag field of the current state and the maximum torque of
+ * the exact effective field; the call stops like mm_relax on that torque,
+ * so the relaxed state meets the same criterion as mm_relax's.  A window
+ * whose start torque is at or below torque_exact (the final approach) runs
+ * on the exact field.  Above it, the surrogate's field of the same state is
+ * checked against the exact one: with a relative L2 residual of at most
+ * `bound` the window's RKF45 stage demag fields come from the surrogate,
+ * otherwise from the exact FFT convolution (a fallback), and the next check
+ * waits 1, 2, 4, ... (at most 64) windows while consecutive checks fail.
+ * MM_F32 context, nz = 1, uniform Ms, surrogate of the same grid (its
+ * launches go to the context's stream for the call).  stats (nullable, 3
+ * longs): exact demag evaluations, surrogate evaluations, failed checks.
+ * Not thread-safe: one call at a time per process. */
 int mm_relax_surrogate(mm_ctx* ctx, mm_fno* f, void* m, double t_max, double torque_tol, long max_steps,
-                       int k_exact, double bound, double* t_out, long* steps_out, long* stats);
+                       int k_exact, double bound, double torque_exact, double* t_out, long* steps_out, long* stats);
 
 /* Energies without a context and without any device allocation.
  *

@@ -97,7 +97,7 @@ def _load():
         "mm_fno_params": (I, [P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
                               ctypes.POINTER(ctypes.c_float)]),
         "mm_fno_set_output_scale": (I, [P, D]),
-        "mm_relax_surrogate": (I, [P, P, P, D, D, L, I, D, DP, LP, LP]),
+        "mm_relax_surrogate": (I, [P, P, P, D, D, L, I, D, D, DP, LP, LP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -443,13 +443,14 @@ def mm_fno_set_output_scale(f, scale):
     _fcheck(_load().mm_fno_set_output_scale(f.handle, float(scale)))
 
 
-def mm_relax_surrogate(ctx, f, m, t_max, torque_tol=1e-4, max_steps=1000000, k_exact=10, bound=1e-3):
+def mm_relax_surrogate(ctx, f, m, t_max, torque_tol=1e-4, max_steps=1000000, k_exact=10, bound=1e-3,
+                       torque_exact=0.0):
     """Returns (t, accepted_steps, exact_evals, surrogate_evals, fallbacks)."""
     tt, ss = ctypes.c_double(0.0), ctypes.c_long(0)
     st = (ctypes.c_long * 3)()
     _check(ctx, _load().mm_relax_surrogate(ctx.handle, f.handle, _dev(ctx, m, ctx.shape3, "m"), float(t_max),
                                            float(torque_tol), int(max_steps), int(k_exact), float(bound),
-                                           ctypes.byref(tt), ctypes.byref(ss), st))
+                                           float(torque_exact), ctypes.byref(tt), ctypes.byref(ss), st))
     return tt.value, ss.value, st[0], st[1], st[2]
 
 

@@ -1,5 +1,6 @@
 // C ABI entry points (include/mm.h): context lifetime, host-side sequencing
 // of the Runge-Kutta stages and of relax(), scalar read-back, state files.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdlib>
@@ -447,7 +448,7 @@ int mm_relax(mm_ctx* ctx, void* m, double t_max, double torque_tol, long max_ste
 }
 
 int mm_relax_surrogate(mm_ctx* ctx, mm_fno* f, void* m, double t_max, double torque_tol, long max_steps,
-                       int k_exact, double bound, double* t_out, long* steps_out, long* stats) {
+                       int k_exact, double bound, double torque_exact, double* t_out, long* steps_out, long* stats) {
     if (!ctx) return fail(nullptr, MM_ERR_INVALID_ARG, "ctx is NULL");
     if (!f || !m || k_exact < 1 || !(t_max > 0) || !(torque_tol >= 0) || max_steps < 0 || !(bound >= 0))
         return fail(ctx, MM_ERR_INVALID_ARG, "surrogate, m, k_exact >= 1, t_max > 0, bounds >= 0 required");
@@ -466,16 +467,15 @@ int mm_relax_surrogate(mm_ctx* ctx, mm_fno* f, void* m, double t_max, double tor
     if ((rc = check_finite_launch(ctx, m))) return rc;
     long exact0 = g_exact_evals, sur0 = g_surrogate_evals, fallbacks = 0, attempts = 0;
     const long max_attempts = 20 * (max_steps + 10);
+    // after a failed residual check the next check waits 1, 2, 4, ... windows
+    // (at most 64), so a surrogate that does not fit the state costs little
+    long skip = 0, backoff = 1;
     rc = MM_OK;
     while (rc == MM_OK) {
-        // window start: exact field, surrogate field, residual, torque
+        // window start: exact field and torque, then (when due) the surrogate's residual
         MM_CUDA_CHECK(ctx, cudaMemsetAsync(&ctx->ctl->torque_bits, 0, sizeof(unsigned long long), ctx->stream));
         ++g_exact_evals;
         if ((rc = demag_apply(ctx, m, ctx->Hs_field))) break;
-        ++g_surrogate_evals;
-        if ((rc = mm_fno_forward(f, m, ctx->Hd, 1))) break;
-        double loss = 0.0;
-        if ((rc = mm_fno_loss(f, ctx->Hd, ctx->Hs_field, nullptr, 1, &loss))) break;
         if ((rc = torque_launch(ctx, m, ctx->Hs_field))) break;
         if ((rc = pull_ctl(ctx))) break;
         if ((rc = device_status(ctx))) break;
@@ -491,10 +491,28 @@ int mm_relax_surrogate(mm_ctx* ctx, mm_fno* f, void* m, double t_max, double tor
                       (long long)c->steps, tq);
             break;
         }
-        const bool use = std::sqrt(loss) <= bound;
-        if (!use) ++fallbacks;
+        const long steps_now = (long)c->steps;
+        bool use = false;
+        if (tq > torque_exact) {   // at or below torque_exact: the final approach is exact
+            if (skip > 0) {
+                --skip;
+            } else {
+                ++g_surrogate_evals;
+                if ((rc = mm_fno_forward(f, m, ctx->Hd, 1))) break;
+                double loss = 0.0;
+                if ((rc = mm_fno_loss(f, ctx->Hd, ctx->Hs_field, nullptr, 1, &loss))) break;
+                use = std::sqrt(loss) <= bound;
+                if (use) {
+                    backoff = 1;
+                } else {
+                    ++fallbacks;
+                    skip = backoff;
+                    backoff = std::min(2 * backoff, 64L);
+                }
+            }
+        }
         g_stage_surrogate = use ? f : nullptr;
-        const long target = c->steps + k_exact;
+        const long target = steps_now + k_exact;
         for (int k = 0; k < 4 * k_exact && rc == MM_OK; ++k, ++attempts) {
             rc = trial(ctx, m, MM_RKF45);
             if (rc == MM_OK && (k + 1) % k_exact == 0) {

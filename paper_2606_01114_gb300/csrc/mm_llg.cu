@@ -195,6 +195,173 @@ __global__ void k_stage(Params<T> p, const T* __restrict__ m_in, const T* __rest
     if constexpr (LAST && METHOD == MM_RKF45) block_max_atomic(err, &ctl->err_bits);
 }
 
+// K7, FP32, uniform material, nx % 4 == 0: four x-consecutive cells per
+// thread with 16-byte loads and stores (the same arithmetic per cell as
+// k_stage; the exchange weights A c_axis / Ms folded once).  Slope pointers
+// travel by value.
+struct KPtrs {
+    float* k[6];
+};
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float& at(float4& v, int j) { return (&v.x)[j]; }
+__device__ __forceinline__ float at(const float4& v, int j) { return (&v.x)[j]; }
+
+struct Cells4 {
+    float4 x, y, z;
+};
+
+__device__ __forceinline__ Cells4 ld_cells(const float* a, long i, long N) {
+    return {ld4(a + i), ld4(a + i + N), ld4(a + i + 2 * N)};
+}
+__device__ __forceinline__ void st_cells(float* a, long i, long N, const Cells4& c) {
+    st4(a + i, c.x);
+    st4(a + i + N, c.y);
+    st4(a + i + 2 * N, c.z);
+}
+// acc += w (nb - c), component-wise over the four cells
+__device__ __forceinline__ void add_diff(Cells4& acc, const Cells4& nb, const Cells4& c, float w) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        at(acc.x, j) += w * (at(nb.x, j) - at(c.x, j));
+        at(acc.y, j) += w * (at(nb.y, j) - at(c.y, j));
+        at(acc.z, j) += w * (at(nb.z, j) - at(c.z, j));
+    }
+}
+
+template <int METHOD, int S>
+__global__ void __launch_bounds__(256) k_stage4(Params<float> p, float wx, float wy, float wz,
+                                                const float* __restrict__ m_in, const float* __restrict__ Hd,
+                                                const float* m0, KPtrs kb, float* m_out, Control* ctl) {
+    constexpr int NS = rk_stages(METHOD);
+    constexpr bool LAST = (S == NS - 1);
+    if (ctl->status != 0 || ctl->done) return;
+    const float dt = (float)ctl->dt;
+    const long i = 4 * ((long)blockIdx.x * blockDim.x + threadIdx.x);
+    const long N = p.N;
+    double err = 0.0;
+    if (i < N) {
+        int x, y, z;
+        decompose(i, p.nx, p.ny, x, y, z);
+        const Cells4 c = ld_cells(m_in, i, N);
+        Cells4 h = {make_float4(0, 0, 0, 0), make_float4(0, 0, 0, 0), make_float4(0, 0, 0, 0)};
+        // x neighbours: inside the quad, plus one cell on each side
+        Cells4 xl, xr;
+        xl.x = make_float4(x > 0 ? m_in[i - 1] : c.x.x, c.x.x, c.x.y, c.x.z);
+        xl.y = make_float4(x > 0 ? m_in[i - 1 + N] : c.y.x, c.y.x, c.y.y, c.y.z);
+        xl.z = make_float4(x > 0 ? m_in[i - 1 + 2 * N] : c.z.x, c.z.x, c.z.y, c.z.z);
+        const bool rx = x + 4 < p.nx;
+        xr.x = make_float4(c.x.y, c.x.z, c.x.w, rx ? m_in[i + 4] : c.x.w);
+        xr.y = make_float4(c.y.y, c.y.z, c.y.w, rx ? m_in[i + 4 + N] : c.y.w);
+        xr.z = make_float4(c.z.y, c.z.z, c.z.w, rx ? m_in[i + 4 + 2 * N] : c.z.w);
+        add_diff(h, xl, c, wx);   // a missing neighbour contributes nb - c = 0
+        add_diff(h, xr, c, wx);
+        const long sy = p.nx, sz = (long)p.nx * p.ny;
+        if (y > 0) add_diff(h, ld_cells(m_in, i - sy, N), c, wy);
+        if (y < p.ny - 1) add_diff(h, ld_cells(m_in, i + sy, N), c, wy);
+        if (z > 0) add_diff(h, ld_cells(m_in, i - sz, N), c, wz);
+        if (z < p.nz - 1) add_diff(h, ld_cells(m_in, i + sz, N), c, wz);
+        const Cells4 d = ld_cells(Hd, i, N);
+        const Cells4 a0 = S == 0 ? c : ld_cells(m0, i, N);
+        Cells4 ks;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const V3<float> mi = {at(c.x, j), at(c.y, j), at(c.z, j)};
+            const V3<float> l = local_at(p, mi, p.Ms);
+            const V3<float> H = {at(h.x, j) + l.x + at(d.x, j), at(h.y, j) + l.y + at(d.y, j),
+                                 at(h.z, j) + l.z + at(d.z, j)};
+            const V3<float> r = llg_rhs(p, mi, H);
+            at(ks.x, j) = r.x;
+            at(ks.y, j) = r.y;
+            at(ks.z, j) = r.z;
+        }
+        if constexpr (!LAST) {
+            Cells4 acc;
+            const float cs = (float)rk_a(METHOD, S + 1, S);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                at(acc.x, j) = cs * at(ks.x, j);
+                at(acc.y, j) = cs * at(ks.y, j);
+                at(acc.z, j) = cs * at(ks.z, j);
+            }
+#pragma unroll
+            for (int q = 0; q < S; ++q) {
+                const float cq = (float)rk_a(METHOD, S + 1, q);
+                if (cq != 0.f) {
+                    const Cells4 kq = ld_cells(kb.k[q], i, N);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        at(acc.x, j) += cq * at(kq.x, j);
+                        at(acc.y, j) += cq * at(kq.y, j);
+                        at(acc.z, j) += cq * at(kq.z, j);
+                    }
+                }
+            }
+            st_cells(kb.k[S], i, N, ks);
+            Cells4 mo;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                at(mo.x, j) = at(a0.x, j) + dt * at(acc.x, j);
+                at(mo.y, j) = at(a0.y, j) + dt * at(acc.y, j);
+                at(mo.z, j) = at(a0.z, j) + dt * at(acc.z, j);
+            }
+            st_cells(m_out, i, N, mo);
+        } else {
+            Cells4 acc = {make_float4(0, 0, 0, 0), make_float4(0, 0, 0, 0), make_float4(0, 0, 0, 0)};
+            Cells4 e = acc;
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                const float cb = (float)rk_b(METHOD, q), ce = (float)rk_e(METHOD, q);
+                if (cb != 0.f || ce != 0.f) {
+                    const Cells4 kq = q == S ? ks : ld_cells(kb.k[q], i, N);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        at(acc.x, j) += cb * at(kq.x, j);
+                        at(acc.y, j) += cb * at(kq.y, j);
+                        at(acc.z, j) += cb * at(kq.z, j);
+                        at(e.x, j) += ce * at(kq.x, j);
+                        at(e.y, j) += ce * at(kq.y, j);
+                        at(e.z, j) += ce * at(kq.z, j);
+                    }
+                }
+            }
+            Cells4 mo;
+            bool bad = false;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float mx = at(a0.x, j) + dt * at(acc.x, j);
+                float my = at(a0.y, j) + dt * at(acc.y, j);
+                float mz = at(a0.z, j) + dt * at(acc.z, j);
+                const float nrm = sqrtf(mx * mx + my * my + mz * mz);
+                if (nrm > 0.f) {
+                    const float inv = 1.f / nrm;
+                    mx *= inv;
+                    my *= inv;
+                    mz *= inv;
+                }
+                bad |= !(isfinite(mx) && isfinite(my) && isfinite(mz));
+                at(mo.x, j) = mx;
+                at(mo.y, j) = my;
+                at(mo.z, j) = mz;
+                if (METHOD == MM_RKF45) {
+                    const double ej = (double)dt * sqrt((double)at(e.x, j) * at(e.x, j) +
+                                                        (double)at(e.y, j) * at(e.y, j) +
+                                                        (double)at(e.z, j) * at(e.z, j));
+                    err = fmax(err, isfinite(ej) ? ej : INFINITY);
+                }
+            }
+            if (METHOD == MM_RKF45) {
+                if (bad) err = INFINITY;
+            } else if (bad) {
+                atomicCAS(&ctl->status, 0, (int)MM_ERR_NONFINITE);
+            }
+            st_cells(m_out, i, N, mo);
+        }
+    }
+    if constexpr (LAST && METHOD == MM_RKF45) block_max_atomic(err, &ctl->err_bits);
+}
+
 // RKF45 step control on the device.
 __global__ void k_controller(Control* ctl, int method) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -312,6 +479,18 @@ inline unsigned blocks_for(long n) { return (unsigned)((n + kThreads - 1) / kThr
 template <typename T, int METHOD, int S>
 int launch_stage(mm_ctx* ctx, const Params<T>& p, const void* m_in, const void* m0, void* m_out, T* const* kdev) {
     KernelTimer kt(ctx, MM_K_STAGE);
+    if constexpr (sizeof(T) == 4) {
+        if (!p.Ms_cell && !p.A_cell && p.Ms != 0.f && p.nx % 4 == 0) {
+            KPtrs kb;
+            for (int s = 0; s < 6; ++s) kb.k[s] = (float*)ctx->k[s];
+            const float inv = 1.f / p.Ms;
+            k_stage4<METHOD, S><<<blocks_for(p.N / 4), kThreads, 0, ctx->stream>>>(
+                p, p.A * p.cx * inv, p.A * p.cy * inv, p.A * p.cz * inv, (const float*)m_in, (const float*)ctx->Hd,
+                (const float*)m0, kb, (float*)m_out, ctx->ctl);
+            MM_LAUNCH_CHECK(ctx);
+            return MM_OK;
+        }
+    }
     k_stage<T, METHOD, S><<<blocks_for(p.N), kThreads, 0, ctx->stream>>>(p, (const T*)m_in, (const T*)ctx->Hd,
                                                                           (const T*)m0, kdev, (T*)m_out, ctx->ctl);
     MM_LAUNCH_CHECK(ctx);

@@ -181,11 +181,11 @@ def test_relax_falls_back_to_exact_field_above_the_bound():
     m0 = torch.tensor(wl.vortex(FILM["n"], FILM["d"]), dtype=torch.float32, device="cuda")
     m = m0.clone()
     t, steps, exact, sur, fb = mm.mm_relax_surrogate(ctx, f, m, 5e-9, torque_tol=1e-2, k_exact=10, bound=1e-3)
-    # every window fell back (the last window start met the torque and ran no
-    # steps): one surrogate evaluation per window start and six exact stage
-    # fields per RKF45 trial besides the window starts' own
-    assert fb == sur - 1 and sur >= 2
-    assert (exact - sur) % 6 == 0 and exact - sur >= 6 * steps
+    # every residual check failed (one surrogate evaluation each, none inside
+    # windows); each RKF45 trial took six exact stage fields besides the
+    # window starts' own
+    assert fb == sur and sur >= 1
+    assert exact - 6 * steps >= 1
     m_ref = m0.clone()
     mm.mm_relax(ctx, m_ref, 5e-9, 1e-2)
     E, E_ref = mm.mm_energy(ctx, m), mm.mm_energy(ctx, m_ref)
@@ -201,8 +201,8 @@ def test_relax_uses_the_surrogate_within_the_bound():
     m = torch.tensor(wl.vortex(FILM["n"], FILM["d"]), dtype=torch.float32, device="cuda")
     t, steps, exact, sur, fb = mm.mm_relax_surrogate(ctx, f, m, 2e-12, torque_tol=0.0, k_exact=5, bound=1e30)
     assert fb == 0 and steps > 0 and t >= 2e-12
-    windows = exact
-    assert sur >= windows + 6 * steps
+    # one exact field per window start; every RKF45 trial on the surrogate
+    assert sur >= exact - 1 + 6 * steps
     norm = torch.linalg.vector_norm(m, dim=0)
     assert torch.all(torch.isfinite(m)) and float((norm - 1).abs().max()) < 1e-5
     mm.mm_fno_destroy(f)
