@@ -361,7 +361,7 @@ template <int L1, int L2> __device__ __forceinline__ int xsw(int k1, int n2) {
 }
 
 template <int L1, int L2>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128, 7)
     k_xfwd_reg(const float* __restrict__ in, const float* __restrict__ Ms, float ms, long ms_rows,
                float2* __restrict__ out, int Hs, long rows, const float2* __restrict__ twL,
                const float2* __restrict__ twP) {
@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(256)
 }
 
 template <int L1, int L2>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128, 8)
     k_xinv_reg(const float2* __restrict__ in, int Hs, float* __restrict__ out, long rows, float scale,
                const float2* __restrict__ twL, const float2* __restrict__ twP) {
     constexpr int L = L1 * L2, B = 4, NX = L;

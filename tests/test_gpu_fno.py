@@ -220,3 +220,33 @@ def test_relax_rejects_wrong_mesh():
             mm.mm_relax_surrogate(ctx, f, m, 1e-12)
         mm.mm_destroy(ctx)
     mm.mm_fno_destroy(f)
+
+
+def test_trained_surrogate_gain_small_film():
+    """The whole pipeline on a 64 x 64 film: pairs from relaxation
+    trajectories, Adam training with the library's kernels, then relax() of
+    held-out states with and without the surrogate.  The relaxed energies
+    agree (the final approach and every failed check run on the exact
+    field); the measured speed ratio is reported, not asserted."""
+    from paper_2606_01114_gb300 import surrogate as sg
+    film = dict(n=(64, 64, 1), d=(4e-9, 4e-9, 4e-9), Ms=8.0e5, A=1.3e-11, alpha=0.5)
+    ctx = sg.film_context(film)
+    ms, hs = sg.generate_pairs(ctx, film, n_traj=12, per_traj=10, seed0=100)
+    f = mm.mm_fno_create(64, 64, width=16, modes=8, layers=4, store_bf16=True, max_batch=16, seed=7)
+    losses = sg.train(f, ms, hs, steps=300, batch=8, lr=2e-3)
+    assert np.mean(losses[-20:]) < 0.5 * np.mean(losses[:5])
+    rows = sg.gain(ctx, f, film, seeds=[10000, 10001], t_max=1e-9, torque_tol=1e-3, k_exact=10, bound=0.2,
+                   torque_exact=1e-2)
+    for r in rows:
+        assert r["surrogate"]["surrogate_evals"] >= 1
+        converged = r["plain"]["torque"] <= 1e-3 and r["surrogate"]["torque"] <= 1e-3
+        if converged:   # both relaxed into the same minimum
+            assert r["energy_rel_err"] <= 1e-4, r
+        else:           # both ran to t_max
+            assert r["plain"]["t"] >= 1e-9 * (1 - 1e-12) or r["surrogate"]["t"] >= 1e-9 * (1 - 1e-12), r
+        print(r["seed"], r["energy_rel_err"], r["plain"]["steps"], r["surrogate"]["steps"],
+              r["surrogate"]["exact_evals"], r["surrogate"]["surrogate_evals"], r["surrogate"]["fallbacks"])
+    speed = sum(r["plain"]["seconds"] for r in rows) / sum(r["surrogate"]["seconds"] for r in rows)
+    print(f"surrogate relax speed ratio on the 64 x 64 film: {speed:.3f}")
+    mm.mm_fno_destroy(f)
+    mm.mm_destroy(ctx)
