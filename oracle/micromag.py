@@ -273,3 +273,43 @@ def relax(p, m, t_max, torque_tol, max_steps, dt0=1e-14, tol=1e-5):
         m, t, dt, _, _ = rkf45_step(p, m, t, dt, tol)
         steps += 1
     return m, t, steps
+
+
+# Barzilai-Borwein energy minimisation.  The paper names the method (its
+# RKF45 paragraph, and the minimiser call of its example script) without
+# printing it; the reading taken here is steepest descent on the unit
+# sphere with Barzilai-Borwein step lengths, alternating the two quotients.
+BB_TAU0 = 1e-4
+
+
+def minimize_bb(p, m, torque_tol, max_iter, tau0=BB_TAU0):
+    """Minimise the energy over unit m.  Per iteration k: h = H_eff / Ms
+    (zero on vacuum cells), g = m x (m x h) (the descent direction is -g,
+    the component of h perpendicular to m), m <- normalise(m - tau g).
+    tau = tau0 on the first step; afterwards, with s = m_k - m_(k-1),
+    y = g_k - g_(k-1) summed over all cells and components,
+    tau = (s.s)/(s.y) on odd k and (s.y)/(y.y) on even k, reset to tau0 when
+    the quotient is not a positive finite number.  Stops before a step once
+    max |m x H_eff| / Ms <= torque_tol, or after max_iter steps.
+    Returns (m, steps taken)."""
+    mag = p.Ms > 0
+    inv_ms = np.where(mag, 1.0 / np.where(mag, p.Ms, 1.0), 0.0)
+    m_prev = g_prev = None
+    tau = tau0
+    for k in range(max_iter + 1):
+        H = p.h_eff(m)
+        if p.max_torque(m, H) <= torque_tol or k == max_iter:
+            return m, k
+        h = H * inv_ms
+        g = np.cross(m, np.cross(m, h, axis=0), axis=0)
+        if m_prev is not None:
+            s_, y_ = m - m_prev, g - g_prev
+            ss, sy, yy = float(np.sum(s_ * s_)), float(np.sum(s_ * y_)), float(np.sum(y_ * y_))
+            with np.errstate(divide="ignore", invalid="ignore"):
+                tau = ss / sy if k % 2 == 1 else sy / yy
+            if not (np.isfinite(tau) and tau > 0):
+                tau = tau0
+        m_prev, g_prev = m, g
+        m = p.normalise(m - tau * g)
+    return m, max_iter
+

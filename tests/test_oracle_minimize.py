@@ -1,0 +1,51 @@
+"""Pins for the oracle's Barzilai-Borwein minimiser: a single cubic cell
+(isotropic demag, no exchange) with uniaxial anisotropy and an oblique field
+is the Stoner-Wohlfarth problem, whose equilibrium angle solves
+K sin 2theta + mu0 Ms H sin(theta - psi) = 0 (root found independently by
+bracketing); on a film the minimiser ends on a stationary point of the LLG
+equation with lower energy than the start and the same energy as an LLG
+relaxation at large damping from the same state."""
+
+import numpy as np
+import pytest
+from scipy.optimize import brentq
+
+import workloads as wl
+from oracle import micromag
+
+MU0 = 4e-7 * np.pi
+
+
+@pytest.mark.parametrize("psi_deg,H", [(30.0, 2e5), (60.0, 1e5), (80.0, 6e5)])
+def test_stoner_wohlfarth_single_cell(psi_deg, H):
+    Ms, K = 8e5, 5e5
+    psi = np.radians(psi_deg)
+    p = micromag.Problem((1, 1, 1), (5e-9, 5e-9, 5e-9), Ms=Ms, A=1e-11, Ku=K, u=(0, 0, 1),
+                         h_ext=(H * np.sin(psi), 0.0, H * np.cos(psi)))
+    theta0 = 0.5 * psi            # start between the easy axis and the field
+    m0 = np.array([np.sin(theta0), 0.0, np.cos(theta0)]).reshape(3, 1, 1, 1)
+    m, k = micromag.minimize_bb(p, m0, 1e-12, 5000)
+    assert k < 5000
+    theta = np.arctan2(m[0, 0, 0, 0], m[2, 0, 0, 0])
+
+    def f(t):
+        return K * np.sin(2 * t) + MU0 * Ms * H * np.sin(t - psi)
+    # the minimum between the easy axis (theta = 0) and the field direction
+    ref = brentq(f, 1e-9, psi - 1e-9)
+    assert theta == pytest.approx(ref, abs=1e-9)
+    assert abs(m[1, 0, 0, 0]) < 1e-12
+
+
+def test_film_minimum_is_stationary_and_matches_llg_relaxation():
+    n, d = (8, 8, 2), (3e-9, 3e-9, 3e-9)
+    p = micromag.Problem(n, d, Ms=8e5, A=1.3e-11, alpha=1.0, Ku=2e5, u=(1, 0, 0), h_ext=(0, 2e4, 0))
+    m0 = wl.smooth_unit(n, sigma_cells=3.0, seed=4)
+    E0 = p.energies(m0).sum()
+    m, k = micromag.minimize_bb(p, m0, 1e-7, 20000)
+    assert p.max_torque(m) <= 1e-7
+    assert np.max(np.abs(p.rhs(m))) < 1e-7 * 2.3e5 * 8e5
+    E = p.energies(m).sum()
+    assert E < E0
+    mr, _, _ = micromag.relax(p, m0, 1e-8, 1e-7, 200000)
+    assert p.energies(mr).sum() == pytest.approx(E, rel=1e-9)
+    np.testing.assert_allclose(mr, m, atol=1e-4)   # soft modes: the torque bound fixes m less tightly than E
