@@ -278,17 +278,19 @@ def relax(p, m, t_max, torque_tol, max_steps, dt0=1e-14, tol=1e-5):
 # Barzilai-Borwein energy minimisation.  The paper names the method (its
 # RKF45 paragraph, and the minimiser call of its example script) without
 # printing it; the reading taken here is steepest descent on the unit
-# sphere with Barzilai-Borwein step lengths, alternating the two quotients.
-BB_TAU0 = 1e-4
+# sphere with Barzilai-Borwein step lengths, alternating the two quotients,
+# and a full step (tau_max) where the path meets non-positive curvature
+# (resetting to the small first step there stalls on saddles).
+BB_TAU0, BB_TAU_MAX = 1e-4, 1.0
 
 
-def minimize_bb(p, m, torque_tol, max_iter, tau0=BB_TAU0):
+def minimize_bb(p, m, torque_tol, max_iter, tau0=BB_TAU0, tau_max=BB_TAU_MAX):
     """Minimise the energy over unit m.  Per iteration k: h = H_eff / Ms
     (zero on vacuum cells), g = m x (m x h) (the descent direction is -g,
     the component of h perpendicular to m), m <- normalise(m - tau g).
     tau = tau0 on the first step; afterwards, with s = m_k - m_(k-1),
     y = g_k - g_(k-1) summed over all cells and components,
-    tau = (s.s)/(s.y) on odd k and (s.y)/(y.y) on even k, reset to tau0 when
+    tau = (s.s)/(s.y) on odd k and (s.y)/(y.y) on even k, or tau_max when
     the quotient is not a positive finite number.  Stops before a step once
     max |m x H_eff| / Ms <= torque_tol, or after max_iter steps.
     Returns (m, steps taken)."""
@@ -308,8 +310,7 @@ def minimize_bb(p, m, torque_tol, max_iter, tau0=BB_TAU0):
             with np.errstate(divide="ignore", invalid="ignore"):
                 tau = ss / sy if k % 2 == 1 else sy / yy
             if not (np.isfinite(tau) and tau > 0):
-                tau = tau0
+                tau = tau_max
         m_prev, g_prev = m, g
         m = p.normalise(m - tau * g)
     return m, max_iter
-
