@@ -120,6 +120,20 @@ int mm_llg_step(mm_ctx* ctx, void* m, double* t, double* dt, int method, double 
 int mm_relax(mm_ctx* ctx, void* m, double t_max, double torque_tol, long max_steps,
              double* t_out, long* steps_out);
 
+/* Energy minimisation by Barzilai-Borwein steepest descent on the unit
+ * sphere (the paper's minimiser, named in its Implementation section beside
+ * RKF45 and called before the LLG run in its example script; the algorithm
+ * is not printed there, this is the reading taken).  Per step, with
+ * h = H_eff / Ms: g = m x (m x h), m <- normalise(m - tau g); tau = 1e-4 on
+ * the first step, then (s.s)/(s.y) on odd and (s.y)/(y.y) on even steps
+ * (s, y the changes of m and g over all cells), 1 where the quotient is not
+ * positive.  Stops before a step once max |m x H_eff| / Ms <= torque_tol
+ * (tested every step on the device) or after max_iter steps; *iters_out
+ * (nullable) receives the steps taken.  m (device, in place) holds the last
+ * state in either case.  Uses the integrator's scratch buffers.  Errors:
+ * NOT_CONVERGED (max_iter reached first), NONFINITE, INVALID_ARG, CUDA. */
+int mm_minimize_bb(mm_ctx* ctx, void* m, double torque_tol, long max_iter, long* iters_out);
+
 /* E_out[0..3] = demag, exchange, anisotropy, Zeeman energy of m in J
  * (float64 accumulation on the device). */
 int mm_energy(mm_ctx* ctx, const void* m, double E_out[4]);

@@ -97,6 +97,7 @@ def _load():
         "mm_fno_params": (I, [P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
                               ctypes.POINTER(ctypes.c_float)]),
         "mm_fno_set_output_scale": (I, [P, D]),
+        "mm_minimize_bb": (I, [P, P, D, L, LP]),
         "mm_relax_surrogate": (I, [P, P, P, D, D, L, I, D, D, DP, LP, LP]),
     }
     for name, (res, args) in sig.items():
@@ -221,6 +222,14 @@ def mm_relax(ctx, m, t_max, torque_tol=1e-4, max_steps=1000000):
     _check(ctx, _load().mm_relax(ctx.handle, _dev(ctx, m, ctx.shape3, "m"), float(t_max), float(torque_tol),
                                  int(max_steps), ctypes.byref(tt), ctypes.byref(ss)))
     return tt.value, ss.value
+
+
+def mm_minimize_bb(ctx, m, torque_tol=1e-4, max_iter=100000):
+    """Barzilai-Borwein energy minimisation of m in place; returns the steps taken."""
+    it = ctypes.c_long(0)
+    _check(ctx, _load().mm_minimize_bb(ctx.handle, _dev(ctx, m, ctx.shape3, "m"), float(torque_tol), int(max_iter),
+                                       ctypes.byref(it)))
+    return it.value
 
 
 def mm_energy(ctx, m):

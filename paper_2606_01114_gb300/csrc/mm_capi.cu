@@ -447,6 +447,39 @@ int mm_relax(mm_ctx* ctx, void* m, double t_max, double torque_tol, long max_ste
     }
 }
 
+int mm_minimize_bb(mm_ctx* ctx, void* m, double torque_tol, long max_iter, long* iters_out) {
+    if (!ctx) return fail(nullptr, MM_ERR_INVALID_ARG, "ctx is NULL");
+    MM_BIND(ctx);
+    if (!m) return fail(ctx, MM_ERR_INVALID_ARG, "m must not be NULL");
+    if (!(torque_tol >= 0) || max_iter < 0) return fail(ctx, MM_ERR_INVALID_ARG, "torque_tol >= 0, max_iter >= 0 required");
+    int rc;
+    if ((rc = sync(ctx))) return rc;
+    reset_ctl(ctx->ctl_host, 0.0, 0.0, 0.0, 0.0);
+    if ((rc = push_ctl(ctx))) return rc;
+    if ((rc = check_finite_launch(ctx, m))) return rc;
+    // slope buffers of the integrator serve as g (two, alternating) and m_prev
+    void* gb[2] = {ctx->k[0], ctx->k[1]};
+    void* m_prev = ctx->k[2];
+    const int kCheck = 10;
+    for (long it = 0;; ++it) {
+        if ((rc = demag_apply(ctx, m, ctx->Hd))) return rc;
+        if ((rc = bb_iteration(ctx, m, gb[it & 1], gb[(it + 1) & 1], m_prev, it > 0, torque_tol, max_iter))) return rc;
+        if ((it + 1) % kCheck == 0 || it >= max_iter) {
+            if ((rc = pull_ctl(ctx))) return rc;
+            if ((rc = device_status(ctx))) return rc;
+            if (ctx->ctl_host->done) break;
+        }
+    }
+    const Control* c = ctx->ctl_host;
+    if (iters_out) *iters_out = (long)c->steps;
+    double tq;
+    unsigned long long bits = c->torque_bits;
+    memcpy(&tq, &bits, sizeof(tq));
+    if (!(tq <= torque_tol))
+        return fail(ctx, MM_ERR_NOT_CONVERGED, "minimiser stopped after %lld steps, torque %.3e", (long long)c->steps, tq);
+    return MM_OK;
+}
+
 int mm_relax_surrogate(mm_ctx* ctx, mm_fno* f, void* m, double t_max, double torque_tol, long max_steps,
                        int k_exact, double bound, double torque_exact, double* t_out, long* steps_out, long* stats) {
     if (!ctx) return fail(nullptr, MM_ERR_INVALID_ARG, "ctx is NULL");

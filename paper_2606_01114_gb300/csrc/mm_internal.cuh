@@ -43,6 +43,7 @@ struct Control {
     unsigned long long err_bits;     // max error of the trial (double bits, >= 0)
     unsigned long long torque_bits;  // max torque / Ms (double bits)
     double energy[4];    // demag, exchange, anisotropy, Zeeman
+    double bb[3];        // minimiser: sums s.s, s.y, y.y
     int accepted;        // 1 if the last trial was accepted
     int status;          // 0 or an MM_ERR_* code raised on the device
     int done;            // relax(): t reached t_max
@@ -190,7 +191,11 @@ int torque_launch(mm_ctx* ctx, const void* m, const void* Hd);   // max into ctl
 int rk_stage(mm_ctx* ctx, int method, int s, const void* m_in, const void* m0, void* m_out);
 int rk_controller(mm_ctx* ctx, int method);            // accept / reject, dt
 int rk_commit(mm_ctx* ctx, void* m0);                  // m0 <- mnext if accepted
-int check_finite_launch(mm_ctx* ctx, const void* m);            // flags ctl->status
+int check_finite_launch(mm_ctx* ctx, const void* m);
+// One Barzilai-Borwein iteration after the demag field of m is in ctx->Hd:
+// gradient, step length and update (no-ops once ctl->done is set).
+int bb_iteration(mm_ctx* ctx, void* m, void* g, const void* g_prev, void* m_prev, bool have_prev,
+                 double torque_tol, long max_iter);            // flags ctl->status
 // host helpers shared with the adjoint (mm_capi.cu)
 int ctl_reset_push(mm_ctx* ctx, double t, double dt, double t_max, double tol);
 int ctl_pull(mm_ctx* ctx);

@@ -476,6 +476,98 @@ __global__ void k_finite(long n3, const T* __restrict__ m, Control* ctl) {
 constexpr int kThreads = 256;
 inline unsigned blocks_for(long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
+// ------------------------------------------------ Barzilai-Borwein minimiser
+// Steepest descent on the unit sphere with Barzilai-Borwein step lengths
+// (the paper's minimiser, named beside RKF45 in its Implementation section):
+// g = m x (m x h), h = H_eff / Ms; m <- normalise(m - tau g).  tau: 1e-4 on
+// the first step, then (s.s)/(s.y) on odd and (s.y)/(y.y) on even steps
+// (s = m_k - m_(k-1), y = g_k - g_(k-1), sums over all cells), or 1 where
+// the quotient is not positive.  The step length and the stop test
+// (max |m x H_eff| / Ms <= tol before a step) are taken on the device.
+constexpr double kBBTau0 = 1e-4, kBBTauMax = 1.0;
+
+template <typename T>
+__global__ void k_bb_grad(Params<T> p, const T* __restrict__ m, const T* __restrict__ Hd, T* __restrict__ g,
+                          const T* __restrict__ g_prev, const T* __restrict__ m_prev, int have_prev, Control* ctl) {
+    if (ctl->status != 0 || ctl->done) return;
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    double tq = 0.0, ss = 0.0, sy = 0.0, yy = 0.0;
+    if (i < p.N) {
+        int x, y, z;
+        decompose(i, p.nx, p.ny, x, y, z);
+        const T Msi = p.Ms_cell ? p.Ms_cell[i] : p.Ms;
+        V3<T> gi = {0, 0, 0};
+        const V3<T> mi = load3(m, i, p.N);
+        if (Msi != (T)0) {
+            const V3<T> hx = exchange_at(p, m, i, x, y, z, mi, Msi);
+            const V3<T> l = local_at(p, mi, Msi);
+            const V3<T> d = load3(Hd, i, p.N);
+            const T inv = (T)1 / Msi;
+            const V3<T> h = {(hx.x + l.x + d.x) * inv, (hx.y + l.y + d.y) * inv, (hx.z + l.z + d.z) * inv};
+            const V3<T> a = {mi.y * h.z - mi.z * h.y, mi.z * h.x - mi.x * h.z, mi.x * h.y - mi.y * h.x};   // m x h
+            gi = {mi.y * a.z - mi.z * a.y, mi.z * a.x - mi.x * a.z, mi.x * a.y - mi.y * a.x};            // m x (m x h)
+            tq = sqrt((double)a.x * a.x + (double)a.y * a.y + (double)a.z * a.z);
+            if (!isfinite(tq)) tq = 1e300;
+        }
+        if (have_prev) {
+            const V3<T> mp = load3(m_prev, i, p.N), gp = load3(g_prev, i, p.N);
+            const double sx = (double)mi.x - mp.x, sy_ = (double)mi.y - mp.y, sz = (double)mi.z - mp.z;
+            const double yx = (double)gi.x - gp.x, yy_ = (double)gi.y - gp.y, yz = (double)gi.z - gp.z;
+            ss = sx * sx + sy_ * sy_ + sz * sz;
+            sy = sx * yx + sy_ * yy_ + sz * yz;
+            yy = yx * yx + yy_ * yy_ + yz * yz;
+        }
+        store3(g, i, p.N, gi);
+    }
+    block_max_atomic(tq, &ctl->torque_bits);
+    if (have_prev) {
+        __syncthreads();
+        block_sum_atomic(ss, &ctl->bb[0]);
+        __syncthreads();
+        block_sum_atomic(sy, &ctl->bb[1]);
+        __syncthreads();
+        block_sum_atomic(yy, &ctl->bb[2]);
+    }
+}
+
+// stop test and step length; ctl->dt carries tau to the update
+__global__ void k_bb_tau(Control* ctl, double torque_tol, long max_iter) {
+    if (threadIdx.x != 0 || blockIdx.x != 0 || ctl->status != 0 || ctl->done) return;
+    const double tq = __longlong_as_double((long long)ctl->torque_bits);
+    const long k = (long)ctl->steps;
+    if (tq <= torque_tol || k >= max_iter) {
+        ctl->done = 1;
+        return;
+    }
+    double tau = kBBTau0;
+    if (k > 0) {
+        const double q = (k & 1) ? ctl->bb[0] / ctl->bb[1] : ctl->bb[1] / ctl->bb[2];
+        tau = (isfinite(q) && q > 0.0) ? q : kBBTauMax;
+    }
+    ctl->dt = tau;
+    ctl->steps = k + 1;
+    ctl->torque_bits = 0ull;
+    ctl->bb[0] = ctl->bb[1] = ctl->bb[2] = 0.0;
+}
+
+template <typename T>
+__global__ void k_bb_update(Params<T> p, T* __restrict__ m, const T* __restrict__ g, T* __restrict__ m_prev,
+                            const Control* ctl) {
+    if (ctl->status != 0 || ctl->done) return;
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.N) return;
+    const T tau = (T)ctl->dt;
+    const V3<T> mi = load3(m, i, p.N);
+    store3(m_prev, i, p.N, mi);
+    const T Msi = p.Ms_cell ? p.Ms_cell[i] : p.Ms;
+    if (Msi == (T)0) return;   // vacuum cells do not move
+    const V3<T> gi = load3(g, i, p.N);
+    V3<T> mn = {mi.x - tau * gi.x, mi.y - tau * gi.y, mi.z - tau * gi.z};
+    const T nrm = sqrt(mn.x * mn.x + mn.y * mn.y + mn.z * mn.z);
+    if (nrm > (T)0) mn = {mn.x / nrm, mn.y / nrm, mn.z / nrm};
+    store3(m, i, p.N, mn);
+}
+
 template <typename T, int METHOD, int S>
 int launch_stage(mm_ctx* ctx, const Params<T>& p, const void* m_in, const void* m0, void* m_out, T* const* kdev) {
     KernelTimer kt(ctx, MM_K_STAGE);
@@ -591,6 +683,26 @@ int rk_commit(mm_ctx* ctx, void* m0) {
         k_commit<float><<<blocks_for(n3), kThreads, 0, ctx->stream>>>(n3, (const float*)ctx->mnext, (float*)m0, ctx->ctl);
     MM_LAUNCH_CHECK(ctx);
     return MM_OK;
+}
+
+template <typename T>
+int bb_iteration_t(mm_ctx* ctx, void* m, void* g, const void* g_prev, void* m_prev, bool have_prev, double tol,
+                   long max_iter) {
+    KernelTimer kt(ctx, MM_K_REDUCE);
+    const Params<T> p = make_params<T>(ctx);
+    k_bb_grad<T><<<blocks_for(p.N), kThreads, 0, ctx->stream>>>(p, (const T*)m, (const T*)ctx->Hd, (T*)g,
+                                                                (const T*)g_prev, (const T*)m_prev, have_prev ? 1 : 0,
+                                                                ctx->ctl);
+    k_bb_tau<<<1, 32, 0, ctx->stream>>>(ctx->ctl, tol, max_iter);
+    k_bb_update<T><<<blocks_for(p.N), kThreads, 0, ctx->stream>>>(p, (T*)m, (const T*)g, (T*)m_prev, ctx->ctl);
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+
+int bb_iteration(mm_ctx* ctx, void* m, void* g, const void* g_prev, void* m_prev, bool have_prev, double torque_tol,
+                 long max_iter) {
+    return ctx->prec == MM_F64 ? bb_iteration_t<double>(ctx, m, g, g_prev, m_prev, have_prev, torque_tol, max_iter)
+                               : bb_iteration_t<float>(ctx, m, g, g_prev, m_prev, have_prev, torque_tol, max_iter);
 }
 
 int check_finite_launch(mm_ctx* ctx, const void* m) {

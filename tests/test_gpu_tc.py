@@ -68,3 +68,58 @@ def test_fft_mode_rejected_for_fp64():
         mm.mm_set_fft_mode(ctx, mm.MM_TC_TF32)
     assert e.value.code == mm.MM_ERR_INVALID_ARG
     mm.mm_destroy(ctx)
+
+
+def test_cube256_per_field_errors_and_speed():
+    """256^3 bulk cube, 1 nm cells, Ku 5e5 along z, random m: relative L2 of
+    each field (demag, exchange, effective, and the torque m x H_eff) for plain FP32 and the two tensor-core modes against the
+    float64 GPU path (itself pinned to the oracle at 1e-12), and the demag
+    time per evaluation of each mode (printed)."""
+    import workloads as wl
+    n, d = (256, 256, 256), (1e-9, 1e-9, 1e-9)
+    m = wl.random_unit(n, seed=11)
+
+    def fields(prec, mode=0):
+        ctx = mm.mm_init_mesh(*n, *d, precision=prec)
+        mm.mm_set_material(ctx, 8e5, 1.3e-11, 0.02, 5e5, (0, 0, 1))
+        if mode:
+            mm.mm_set_fft_mode(ctx, mode)
+        dt = torch.float64 if prec == mm.MM_F64 else torch.float32
+        md = torch.tensor(m, dtype=dt, device="cuda")
+        out = {}
+        Hd, Hx, He = torch.empty_like(md), torch.empty_like(md), torch.empty_like(md)
+        mm.mm_demag_field(ctx, md, Hd)
+        mm.mm_exchange_field(ctx, md, Hx)
+        mm.mm_effective_field(ctx, md, He)
+        if mode:
+            mm.mm_tc_status(ctx)
+        out["demag"], out["exchange"], out["effective"] = Hd.double(), Hx.double(), He.double()
+        out["torque"] = torch.linalg.cross(md.double(), He.double(), dim=0)
+        # demag time per evaluation
+        for _ in range(3):
+            mm.mm_demag_field(ctx, md, Hd)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(10):
+            mm.mm_demag_field(ctx, md, Hd)
+        b.record()
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) / 10
+        mm.mm_destroy(ctx)
+        return out, t
+
+    ref, t64 = fields(mm.MM_F64)
+    rows = {}
+    for name, prec, mode in (("fp32", mm.MM_F32, 0), ("tf32x2", mm.MM_F32, mm.MM_TC_TF32),
+                             ("bf16x3", mm.MM_F32, mm.MM_TC_BF16)):
+        out, t = fields(prec, mode)
+        errs = {k: float(torch.linalg.vector_norm(out[k] - ref[k]) / torch.linalg.vector_norm(ref[k])) for k in ref}
+        rows[name] = (errs, t)
+        print(name, f"demag {t:.3f} ms/eval", {k: f"{v:.2e}" for k, v in errs.items()})
+    print(f"fp64 demag {t64:.3f} ms/eval")
+    assert rows["fp32"][0]["demag"] < 1e-5 and rows["fp32"][0]["effective"] < 1e-5
+    assert rows["tf32x2"][0]["demag"] < 1e-5
+    assert rows["bf16x3"][0]["demag"] < 1e-4
+    del ref
+    torch.cuda.empty_cache()
