@@ -32,7 +32,7 @@ class Problem:
     """Mesh + material: the state an ``mm_ctx`` holds on the GPU side."""
 
     def __init__(self, n, d, Ms=8e5, A=1.3e-11, alpha=0.02, Ku=0.0, u=(0.0, 0.0, 1.0),
-                 h_ext=(0.0, 0.0, 0.0), Ms_cell=None, A_cell=None):
+                 h_ext=(0.0, 0.0, 0.0), Ms_cell=None, A_cell=None, D=0.0, dmi="interfacial"):
         self.n = tuple(int(v) for v in n)
         self.d = tuple(float(v) for v in d)
         nx, ny, nz = self.n
@@ -44,6 +44,9 @@ class Problem:
         u = np.asarray(u, dtype=np.float64)
         self.u = u / np.linalg.norm(u)
         self.h_ext = np.asarray(h_ext, dtype=np.float64)
+        self.D = float(D)
+        assert dmi in ("interfacial", "bulk")
+        self.dmi_type = dmi
         self._kernel = None
 
     @property
@@ -146,6 +149,68 @@ class Problem:
             pref = np.where(mag, 2.0 / (MU0 * Ms), 0.0)
         return H * pref
 
+    def dmi_vectors(self):
+        """e_k^DMI for k = x, y, z (Eq. 3): (e_y, -e_x, 0) interfacial, (e_x, e_y, e_z) bulk."""
+        ex, ey, ez = np.eye(3)
+        if self.dmi_type == "interfacial":
+            return [ey, -ex, np.zeros(3)]
+        return [ex, ey, ez]
+
+    def dmi(self, m):
+        """Eq. 3 for unit m: H = 2D / (mu0 Ms) sum_k e_k x dm/dk, dm/dk by the
+        central difference (m[+k] - m[-k]) / (2 d_k) with a neighbour outside
+        the magnet (mesh edge or Ms = 0) contributing nothing: the field of the
+        bond energy (D V / d_k) sum_bonds e_k . (m_i x m_(i+k))."""
+        H = np.zeros_like(m, dtype=np.float64)
+        if self.D == 0.0:
+            return H
+        Ms = self.Ms
+        mag = Ms > 0
+        evec = self.dmi_vectors()
+        for k, (axis, h) in enumerate(((2, self.d[0]), (1, self.d[1]), (0, self.d[2]))):
+            e = evec[k]
+            n_ax = Ms.shape[axis]
+            if n_ax == 1 or not e.any():
+                continue
+            for shift in (1, -1):
+                src = [slice(None)] * 3
+                dst = [slice(None)] * 3
+                if shift == 1:
+                    dst[axis], src[axis] = slice(0, n_ax - 1), slice(1, n_ax)
+                else:
+                    dst[axis], src[axis] = slice(1, n_ax), slice(0, n_ax - 1)
+                dst, src = tuple(dst), tuple(src)
+                w = shift * mag[src] * mag[dst] / (2 * h)
+                nb = np.stack([m[c][src] for c in range(3)])
+                cr = np.cross(np.broadcast_to(e[:, None, None, None], nb.shape), nb, axis=0)
+                for c in range(3):
+                    H[c][dst] += w * cr[c]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            pref = np.where(mag, 2.0 * self.D / (MU0 * Ms), 0.0)
+        return H * pref
+
+    def dmi_bond_energy(self, m):
+        """(D V / d_k) sum over bonds (i, i + k) between magnetic cells of
+        e_k . (m_i x m_(i+k)): the energy whose field is Eq. 3 discretised."""
+        if self.D == 0.0:
+            return 0.0
+        mag = self.Ms > 0
+        E = 0.0
+        for k, (axis, h) in enumerate(((2, self.d[0]), (1, self.d[1]), (0, self.d[2]))):
+            e = self.dmi_vectors()[k]
+            n_ax = mag.shape[axis]
+            if n_ax == 1:
+                continue
+            a = [slice(None)] * 3
+            b = [slice(None)] * 3
+            a[axis], b[axis] = slice(0, n_ax - 1), slice(1, n_ax)
+            a, b = tuple(a), tuple(b)
+            mi = np.stack([m[c][a] for c in range(3)])
+            mj = np.stack([m[c][b] for c in range(3)])
+            cr = np.cross(mi, mj, axis=0)
+            E += np.sum((e[0] * cr[0] + e[1] * cr[1] + e[2] * cr[2]) * mag[a] * mag[b]) * self.D * self.V / h
+        return float(E)
+
     def anisotropy(self, m):
         mag = self.Ms > 0
         with np.errstate(divide="ignore", invalid="ignore"):
@@ -159,7 +224,7 @@ class Problem:
 
     def h_eff(self, m, demag=None):
         Hd = self.demag_fft(m) if demag is None else demag
-        return Hd + self.exchange(m) + self.anisotropy(m) + self.zeeman(m)
+        return Hd + self.exchange(m) + self.anisotropy(m) + self.zeeman(m) + self.dmi(m)
 
     # --------------------------------------------------------------- LLG
     def llg_rhs(self, m, H):
@@ -206,7 +271,7 @@ class Problem:
 
     # ---------------------------------------------------------- energies
     def energies(self, m):
-        """(E_demag, E_exchange, E_anisotropy, E_zeeman) in J."""
+        """(E_demag, E_exchange, E_anisotropy, E_zeeman, E_dmi) in J."""
         V = self.V
         Ms = self.Ms
         e_d = -0.5 * MU0 * V * np.sum(Ms * np.sum(m * self.demag_fft(m), axis=0))
@@ -214,7 +279,8 @@ class Problem:
         mu = self.u[0] * m[0] + self.u[1] * m[1] + self.u[2] * m[2]
         e_a = -self.Ku * V * np.sum((Ms > 0) * mu * mu)
         e_z = -MU0 * V * np.sum(Ms * np.sum(m * self.zeeman(m), axis=0))
-        return np.array([e_d, e_x, e_a, e_z])
+        e_m = -0.5 * MU0 * V * np.sum(Ms * np.sum(m * self.dmi(m), axis=0))
+        return np.array([e_d, e_x, e_a, e_z, e_m])
 
     def max_torque(self, m, H=None):
         """max over magnetic cells of |m x H_eff| / Ms (dimensionless)."""
