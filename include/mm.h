@@ -45,6 +45,7 @@ typedef struct mm_ctx mm_ctx;
 
 enum { MM_F32 = 0, MM_F64 = 1 };
 enum { MM_RK4 = 0, MM_RKF45 = 1 };
+enum { MM_DMI_INTERFACIAL = 1, MM_DMI_BULK = 2 };
 
 enum {
     MM_OK = 0,
@@ -90,6 +91,18 @@ int mm_set_material_fields(mm_ctx* ctx, const void* Ms_cell, const void* A_cell)
 /* Uniform external (Zeeman) field in A/m. */
 int mm_set_external_field(mm_ctx* ctx, double hx, double hy, double hz);
 
+/* Dzyaloshinskii-Moriya interaction (Eq. 3, unit m):
+ *   H = 2 D / (mu0 Ms) sum_k e_k x dm/dk,
+ * e_k = (e_y, -e_x, 0) for MM_DMI_INTERFACIAL, (e_x, e_y, e_z) for
+ * MM_DMI_BULK; D in J/m^2 (0 switches it off).  dm/dk is the central
+ * difference, and a neighbour outside the magnet (mesh edge or Ms = 0)
+ * contributes nothing: the field is that of the bond energy
+ * (D V / d_k) sum_bonds e_k . (m_i x m_(i+k)), which mm_energy reports as
+ * E_out[4].  Enters the effective field, the LLG stages, the torque, the
+ * energies and the minimiser; the adjoint entry points reject D != 0.
+ * Errors: INVALID_ARG. */
+int mm_set_dmi(mm_ctx* ctx, double D, int type);
+
 /* H = demagnetisation field of m (Eq. 4), both device [3][nz][ny][nx]. */
 int mm_demag_field(mm_ctx* ctx, const void* m, void* H);
 
@@ -134,9 +147,9 @@ int mm_relax(mm_ctx* ctx, void* m, double t_max, double torque_tol, long max_ste
  * NOT_CONVERGED (max_iter reached first), NONFINITE, INVALID_ARG, CUDA. */
 int mm_minimize_bb(mm_ctx* ctx, void* m, double torque_tol, long max_iter, long* iters_out);
 
-/* E_out[0..3] = demag, exchange, anisotropy, Zeeman energy of m in J
+/* E_out[0..4] = demag, exchange, anisotropy, Zeeman, DMI energy of m in J
  * (float64 accumulation on the device). */
-int mm_energy(mm_ctx* ctx, const void* m, double E_out[4]);
+int mm_energy(mm_ctx* ctx, const void* m, double E_out[5]);
 
 /* *out = max over magnetic cells of |m x H_eff| / Ms. */
 int mm_max_torque(mm_ctx* ctx, const void* m, double* out);
@@ -305,7 +318,8 @@ int mm_relax_surrogate(mm_ctx* ctx, mm_fno* f, void* m, double t_max, double tor
  * example code that runs inside a memory pool or arena it does not own, or a
  * plugin that is handed only its host application's buffers), and so cannot
  * create a context.  It computes what mm_energy computes (E_out[0..3] =
- * demag, exchange, anisotropy, Zeeman energy in J) for a uniform material,
+ * demag, exchange, anisotropy, Zeeman energy in J) for a uniform material
+ * without DMI,
  * taking the demagnetisation field H_demag from the caller (for instance
  * from mm_demag_field) instead of evaluating it.
  *   m, H_demag  device arrays [3][nz][ny][nx] of the given precision

@@ -19,6 +19,7 @@ import numpy as np
 
 MM_F32, MM_F64 = 0, 1
 MM_RK4, MM_RKF45 = 0, 1
+MM_DMI_INTERFACIAL, MM_DMI_BULK = 1, 2
 MM_OK = 0
 MM_ERR_INVALID_ARG = -1
 MM_ERR_CUDA = -2
@@ -97,6 +98,7 @@ def _load():
         "mm_fno_params": (I, [P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
                               ctypes.POINTER(ctypes.c_float)]),
         "mm_fno_set_output_scale": (I, [P, D]),
+        "mm_set_dmi": (I, [P, D, I]),
         "mm_minimize_bb": (I, [P, P, D, L, LP]),
         "mm_relax_surrogate": (I, [P, P, P, D, D, L, I, D, D, DP, LP, LP]),
     }
@@ -196,6 +198,10 @@ def mm_set_external_field(ctx, hx, hy, hz):
     _check(ctx, _load().mm_set_external_field(ctx.handle, float(hx), float(hy), float(hz)))
 
 
+def mm_set_dmi(ctx, D, kind=MM_DMI_INTERFACIAL):
+    _check(ctx, _load().mm_set_dmi(ctx.handle, float(D), int(kind)))
+
+
 def mm_demag_field(ctx, m, H):
     _check(ctx, _load().mm_demag_field(ctx.handle, _dev(ctx, m, ctx.shape3, "m"), _dev(ctx, H, ctx.shape3, "H")))
 
@@ -233,7 +239,7 @@ def mm_minimize_bb(ctx, m, torque_tol=1e-4, max_iter=100000):
 
 
 def mm_energy(ctx, m):
-    E = (ctypes.c_double * 4)()
+    E = (ctypes.c_double * 5)()
     _check(ctx, _load().mm_energy(ctx.handle, _dev(ctx, m, ctx.shape3, "m"), E))
     return np.array(E[:])
 

@@ -447,6 +447,15 @@ int mm_relax(mm_ctx* ctx, void* m, double t_max, double torque_tol, long max_ste
     }
 }
 
+int mm_set_dmi(mm_ctx* ctx, double D, int type) {
+    if (!ctx) return fail(nullptr, MM_ERR_INVALID_ARG, "ctx is NULL");
+    if (!std::isfinite(D) || (type != MM_DMI_INTERFACIAL && type != MM_DMI_BULK))
+        return fail(ctx, MM_ERR_INVALID_ARG, "DMI: finite D and type MM_DMI_INTERFACIAL or MM_DMI_BULK required");
+    ctx->D = D;
+    ctx->dmi_type = type;
+    return MM_OK;
+}
+
 int mm_minimize_bb(mm_ctx* ctx, void* m, double torque_tol, long max_iter, long* iters_out) {
     if (!ctx) return fail(nullptr, MM_ERR_INVALID_ARG, "ctx is NULL");
     MM_BIND(ctx);
@@ -566,16 +575,16 @@ int mm_relax_surrogate(mm_ctx* ctx, mm_fno* f, void* m, double t_max, double tor
     return rc;
 }
 
-int mm_energy(mm_ctx* ctx, const void* m, double E_out[4]) {
+int mm_energy(mm_ctx* ctx, const void* m, double E_out[5]) {
     if (!ctx) return fail(nullptr, MM_ERR_INVALID_ARG, "ctx is NULL");
     MM_BIND(ctx);
     if (!m || !E_out) return fail(ctx, MM_ERR_INVALID_ARG, "m and E_out must not be NULL");
     int rc;
-    MM_CUDA_CHECK(ctx, cudaMemsetAsync(ctx->ctl->energy, 0, 4 * sizeof(double), ctx->stream));
+    MM_CUDA_CHECK(ctx, cudaMemsetAsync(ctx->ctl->energy, 0, 5 * sizeof(double), ctx->stream));
     if ((rc = demag_apply(ctx, m, ctx->Hd))) return rc;
     if ((rc = energy_launch(ctx, m, ctx->Hd))) return rc;
     if ((rc = pull_ctl(ctx))) return rc;
-    for (int i = 0; i < 4; ++i) E_out[i] = ctx->ctl_host->energy[i];
+    for (int i = 0; i < 5; ++i) E_out[i] = ctx->ctl_host->energy[i];
     return MM_OK;
 }
 

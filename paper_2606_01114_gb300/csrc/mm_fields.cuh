@@ -20,6 +20,8 @@ template <typename T> struct Params {
     T hx, hy, hz;
     T pref;             // -gamma / (1 + alpha^2)
     T alpha;
+    int dmi;            // 0 none, 1 interfacial, 2 bulk
+    T dx_c, dy_c, dz_c; // D / (mu0 d) per axis
 };
 
 template <typename T>
@@ -45,6 +47,10 @@ inline Params<T> make_params(const mm_ctx* ctx) {
     p.hz = (T)ctx->hext[2];
     p.pref = (T)(-kGamma / (1.0 + ctx->alpha * ctx->alpha));
     p.alpha = (T)ctx->alpha;
+    p.dmi = ctx->D != 0.0 ? ctx->dmi_type : 0;
+    p.dx_c = (T)(ctx->D / (kMu0 * ctx->dx));
+    p.dy_c = (T)(ctx->D / (kMu0 * ctx->dy));
+    p.dz_c = (T)(ctx->D / (kMu0 * ctx->dz));
     return p;
 }
 
@@ -100,6 +106,51 @@ __device__ __forceinline__ V3<T> local_at(const Params<T>& p, V3<T> mi, T Msi) {
     T mu = mi.x * p.ux + mi.y * p.uy + mi.z * p.uz;
     T k = p.anis / Msi * mu;
     return {k * p.ux + p.hx, k * p.uy + p.hy, k * p.uz + p.hz};
+}
+
+// DMI field (Eq. 3) at cell i of unit m; Msi > 0:
+//   H = 2 D / (mu0 Ms) sum_k e_k x (m[+k] - m[-k]) / (2 d_k),
+// e_k = (e_y, -e_x, 0) interfacial or (e_x, e_y, e_z) bulk; a neighbour
+// outside the magnet (mesh edge or Ms = 0) contributes nothing (the field
+// of the bond energy (D V / d_k) sum_bonds e_k . (m_i x m_(i+k))).
+template <typename T>
+__device__ __forceinline__ V3<T> dmi_at(const Params<T>& p, const T* __restrict__ m, long i, int x, int y, int z,
+                                        T Msi) {
+    T hx = 0, hy = 0, hz = 0;
+    // sum over the present neighbours of sign * (m_nb) per axis: v_axis
+    auto acc = [&](long j, T sgn, T& vx, T& vy, T& vz) {
+        if (p.Ms_cell && p.Ms_cell[j] == (T)0) return;
+        vx += sgn * m[j];
+        vy += sgn * m[j + p.N];
+        vz += sgn * m[j + 2 * p.N];
+    };
+    const long sx = 1, sy = p.nx, sz = (long)p.nx * p.ny;
+    T ax = 0, ay = 0, az = 0, bx = 0, by = 0, bz = 0, cx = 0, cy = 0, cz = 0;
+    if (x < p.nx - 1) acc(i + sx, (T)1, ax, ay, az);
+    if (x > 0) acc(i - sx, (T)-1, ax, ay, az);
+    if (y < p.ny - 1) acc(i + sy, (T)1, bx, by, bz);
+    if (y > 0) acc(i - sy, (T)-1, bx, by, bz);
+    if (p.dmi == 2) {
+        if (z < p.nz - 1) acc(i + sz, (T)1, cx, cy, cz);
+        if (z > 0) acc(i - sz, (T)-1, cx, cy, cz);
+    }
+    if (p.dmi == 1) {
+        // e_y x a (x axis) and -e_x x b (y axis)
+        hx = p.dx_c * az;
+        hz = -p.dx_c * ax;
+        hy = p.dy_c * bz;
+        hz += -p.dy_c * by;
+    } else {
+        // e_x x a, e_y x b, e_z x c
+        hy = -p.dx_c * az;
+        hz = p.dx_c * ay;
+        hx = p.dy_c * bz;
+        hz += -p.dy_c * bx;
+        hx += -p.dz_c * cy;
+        hy += p.dz_c * cx;
+    }
+    const T inv = (T)1 / Msi;
+    return {hx * inv, hy * inv, hz * inv};
 }
 
 template <typename T>

@@ -42,7 +42,7 @@ struct Control {
     double tol;          // RKF45 tolerance
     unsigned long long err_bits;     // max error of the trial (double bits, >= 0)
     unsigned long long torque_bits;  // max torque / Ms (double bits)
-    double energy[4];    // demag, exchange, anisotropy, Zeeman
+    double energy[5];    // demag, exchange, anisotropy, Zeeman, DMI
     double bb[3];        // minimiser: sums s.s, s.y, y.y
     int accepted;        // 1 if the last trial was accepted
     int status;          // 0 or an MM_ERR_* code raised on the device
@@ -79,6 +79,8 @@ struct mm_ctx {
 
     // material
     double Ms, A, alpha, Ku, u[3], hext[3];
+    double D;                 // DMI constant (J/m^2)
+    int dmi_type;             // 0 none, MM_DMI_INTERFACIAL, MM_DMI_BULK
     bool has_Ms_cell, has_A_cell;
     void* Ms_cell;            // [N] path precision (allocated always; filled when used)
     void* A_cell;

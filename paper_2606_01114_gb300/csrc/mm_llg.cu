@@ -110,6 +110,10 @@ __global__ void k_field(Params<T> p, const T* __restrict__ m, const T* __restric
             V3<T> l = local_at(p, mi, Msi);
             V3<T> d = load3(Hd, i, p.N);
             h = {h.x + l.x + d.x, h.y + l.y + d.y, h.z + l.z + d.z};
+            if (p.dmi) {
+                const V3<T> q = dmi_at(p, m, i, x, y, z, Msi);
+                h = {h.x + q.x, h.y + q.y, h.z + q.z};
+            }
         }
     } else if (MODE == 1) {
         h = load3(Hd, i, p.N);   // vacuum cell: only the stray (demag) field
@@ -138,6 +142,10 @@ __global__ void k_stage(Params<T> p, const T* __restrict__ m_in, const T* __rest
             V3<T> l = local_at(p, mi, Msi);
             V3<T> d = load3(Hd, i, p.N);
             h = {h.x + l.x + d.x, h.y + l.y + d.y, h.z + l.z + d.z};
+            if (p.dmi) {
+                const V3<T> q = dmi_at(p, m_in, i, x, y, z, Msi);
+                h = {h.x + q.x, h.y + q.y, h.z + q.z};
+            }
             ks = llg_rhs(p, mi, h);
         }
         V3<T> a0 = S == 0 ? mi : load3(m0, i, p.N);
@@ -419,7 +427,7 @@ template <typename T>
 __global__ void k_energy(Params<T> p, const T* __restrict__ m, const T* __restrict__ Hd, double V, double mu0,
                          double Ku, Control* ctl) {
     long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    double ed = 0, ex = 0, ea = 0, ez = 0;
+    double ed = 0, ex = 0, ea = 0, ez = 0, em = 0;
     if (i < p.N) {
         int x, y, z;
         decompose(i, p.nx, p.ny, x, y, z);
@@ -434,6 +442,10 @@ __global__ void k_energy(Params<T> p, const T* __restrict__ m, const T* __restri
             double mu = (double)mi.x * p.ux + (double)mi.y * p.uy + (double)mi.z * p.uz;
             ea = -Ku * V * mu * mu;
             ez = -mu0 * V * ms * ((double)mi.x * p.hx + (double)mi.y * p.hy + (double)mi.z * p.hz);
+            if (p.dmi) {
+                const V3<T> q = dmi_at(p, m, i, x, y, z, Msi);
+                em = -0.5 * mu0 * V * ms * ((double)mi.x * q.x + (double)mi.y * q.y + (double)mi.z * q.z);
+            }
         }
     }
     block_sum_atomic(ed, &ctl->energy[0]);
@@ -443,6 +455,8 @@ __global__ void k_energy(Params<T> p, const T* __restrict__ m, const T* __restri
     block_sum_atomic(ea, &ctl->energy[2]);
     __syncthreads();
     block_sum_atomic(ez, &ctl->energy[3]);
+    __syncthreads();
+    block_sum_atomic(em, &ctl->energy[4]);
 }
 
 template <typename T>
@@ -458,7 +472,10 @@ __global__ void k_torque(Params<T> p, const T* __restrict__ m, const T* __restri
             V3<T> h = exchange_at(p, m, i, x, y, z, mi, Msi);
             V3<T> l = local_at(p, mi, Msi);
             V3<T> d = load3(Hd, i, p.N);
-            double Hx = (double)h.x + l.x + d.x, Hy = (double)h.y + l.y + d.y, Hz = (double)h.z + l.z + d.z;
+            V3<T> q = {0, 0, 0};
+            if (p.dmi) q = dmi_at(p, m, i, x, y, z, Msi);
+            double Hx = (double)h.x + l.x + d.x + q.x, Hy = (double)h.y + l.y + d.y + q.y,
+                   Hz = (double)h.z + l.z + d.z + q.z;
             double cx = mi.y * Hz - mi.z * Hy, cy = mi.z * Hx - mi.x * Hz, cz = mi.x * Hy - mi.y * Hx;
             tq = sqrt(cx * cx + cy * cy + cz * cz) / (double)Msi;
             if (!isfinite(tq)) tq = 1e300;
@@ -502,8 +519,11 @@ __global__ void k_bb_grad(Params<T> p, const T* __restrict__ m, const T* __restr
             const V3<T> hx = exchange_at(p, m, i, x, y, z, mi, Msi);
             const V3<T> l = local_at(p, mi, Msi);
             const V3<T> d = load3(Hd, i, p.N);
+            V3<T> q = {0, 0, 0};
+            if (p.dmi) q = dmi_at(p, m, i, x, y, z, Msi);
             const T inv = (T)1 / Msi;
-            const V3<T> h = {(hx.x + l.x + d.x) * inv, (hx.y + l.y + d.y) * inv, (hx.z + l.z + d.z) * inv};
+            const V3<T> h = {(hx.x + l.x + d.x + q.x) * inv, (hx.y + l.y + d.y + q.y) * inv,
+                             (hx.z + l.z + d.z + q.z) * inv};
             const V3<T> a = {mi.y * h.z - mi.z * h.y, mi.z * h.x - mi.x * h.z, mi.x * h.y - mi.y * h.x};   // m x h
             gi = {mi.y * a.z - mi.z * a.y, mi.z * a.x - mi.x * a.z, mi.x * a.y - mi.y * a.x};            // m x (m x h)
             tq = sqrt((double)a.x * a.x + (double)a.y * a.y + (double)a.z * a.z);
@@ -572,7 +592,7 @@ template <typename T, int METHOD, int S>
 int launch_stage(mm_ctx* ctx, const Params<T>& p, const void* m_in, const void* m0, void* m_out, T* const* kdev) {
     KernelTimer kt(ctx, MM_K_STAGE);
     if constexpr (sizeof(T) == 4) {
-        if (!p.Ms_cell && !p.A_cell && p.Ms != 0.f && p.nx % 4 == 0) {
+        if (!p.Ms_cell && !p.A_cell && p.Ms != 0.f && p.nx % 4 == 0 && !p.dmi) {
             KPtrs kb;
             for (int s = 0; s < 6; ++s) kb.k[s] = (float*)ctx->k[s];
             const float inv = 1.f / p.Ms;
