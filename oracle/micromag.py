@@ -26,13 +26,15 @@ from . import newell
 
 MU0 = 4e-7 * np.pi
 GAMMA = 2.2127615e5          # mu0 * gamma_e, m / (A s)
+HBAR = 1.054571817e-34       # J s (exact SI value of h / 2 pi)
+QE = 1.602176634e-19         # C (exact SI value)
 
 
 class Problem:
     """Mesh + material: the state an ``mm_ctx`` holds on the GPU side."""
 
     def __init__(self, n, d, Ms=8e5, A=1.3e-11, alpha=0.02, Ku=0.0, u=(0.0, 0.0, 1.0),
-                 h_ext=(0.0, 0.0, 0.0), Ms_cell=None, A_cell=None, D=0.0, dmi="interfacial"):
+                 h_ext=(0.0, 0.0, 0.0), Ms_cell=None, A_cell=None, D=0.0, dmi="interfacial", stt=None):
         self.n = tuple(int(v) for v in n)
         self.d = tuple(float(v) for v in d)
         nx, ny, nz = self.n
@@ -47,6 +49,14 @@ class Problem:
         self.D = float(D)
         assert dmi in ("interfacial", "bulk")
         self.dmi_type = dmi
+        # Slonczewski spin-transfer torque: dict(J, P, Lambda, eps_prime, p, d) or None
+        self.stt = None
+        if stt is not None:
+            st = dict(stt)
+            pv = np.asarray(st["p"], dtype=np.float64)
+            st["p"] = pv / np.linalg.norm(pv)
+            st.setdefault("d", self.n[2] * self.d[2])
+            self.stt = st
         self._kernel = None
 
     @property
@@ -228,11 +238,37 @@ class Problem:
 
     # --------------------------------------------------------------- LLG
     def llg_rhs(self, m, H):
-        """Eq. 1 for the unit vector m (cells with Ms = 0 do not move)."""
+        """Eq. 1 for the unit vector m (cells with Ms = 0 do not move), plus
+        the Slonczewski torque when configured."""
         mxh = np.cross(m, H, axis=0)
         mxmxh = np.cross(m, mxh, axis=0)
         pref = -GAMMA / (1 + self.alpha ** 2)
-        return pref * (mxh + self.alpha * mxmxh) * (self.Ms > 0)
+        r = pref * (mxh + self.alpha * mxmxh)
+        if self.stt is not None:
+            r = r + self.stt_torque(m)
+        return r * (self.Ms > 0)
+
+    def stt_torque(self, m):
+        """Slonczewski spin-transfer torque (named in the paper as a local
+        term; reading taken): in Gilbert form the term
+        gamma beta [eps m x (p x m) + eps' p x m] is added to Eq. 1 with
+        beta = hbar J / (mu0 e Ms d) (A/m), eps = P L^2 / ((L^2 + 1) + (L^2 - 1) m.p);
+        solved for dm/dt it becomes
+        gamma beta / (1 + alpha^2) [(eps + alpha eps') m x (p x m) - (eps' - alpha eps) m x p]."""
+        st = self.stt
+        pv = st["p"].reshape(3, 1, 1, 1) * np.ones_like(m)
+        mag = self.Ms > 0
+        with np.errstate(divide="ignore", invalid="ignore"):
+            beta = np.where(mag, HBAR * st["J"] / (MU0 * QE * np.where(mag, self.Ms, 1.0) * st["d"]), 0.0)
+        L2 = st["Lambda"] ** 2
+        mp = np.sum(m * pv, axis=0)
+        eps = st["P"] * L2 / ((L2 + 1) + (L2 - 1) * mp)
+        a = self.alpha
+        pxm = np.cross(pv, m, axis=0)
+        mxpxm = np.cross(m, pxm, axis=0)
+        mxp = -pxm
+        c = GAMMA * beta / (1 + a * a)
+        return c * ((eps + a * st["eps_prime"]) * mxpxm - (st["eps_prime"] - a * eps) * mxp)
 
     def rhs(self, m):
         return self.llg_rhs(m, self.h_eff(m))
