@@ -103,6 +103,21 @@ int mm_set_external_field(mm_ctx* ctx, double hx, double hy, double hz);
  * Errors: INVALID_ARG. */
 int mm_set_dmi(mm_ctx* ctx, double D, int type);
 
+/* Slonczewski spin-transfer torque (named in the paper as a local term
+ * beside the effective fields; the form below is the reading taken).  In
+ * Gilbert form the term gamma beta [eps m x (p x m) + eps' p x m] is added
+ * to Eq. 1, beta = hbar J / (mu0 e Ms d) (A/m),
+ * eps = P Lambda^2 / ((Lambda^2 + 1) + (Lambda^2 - 1) m.p); solved for dm/dt:
+ *   gamma beta / (1 + alpha^2) [(eps + alpha eps') m x (p x m) - (eps' - alpha eps) m x p].
+ * J current density (A/m^2; 0 switches the torque off), P polarisation,
+ * Lambda >= 1, eps_prime the field-like coefficient, p[3] the fixed-layer
+ * polarisation (normalised here), d the free-layer thickness in m
+ * (<= 0: nz dz).  Enters the LLG stages only (not the effective field,
+ * energies, torque criterion or minimiser); the adjoint entry points reject
+ * it.  Set alpha with mm_set_material first: the torque's (1 + alpha^2) is
+ * taken at each step from the current material.  Errors: INVALID_ARG. */
+int mm_set_stt(mm_ctx* ctx, double J, double P, double Lambda, double eps_prime, const double p[3], double d);
+
 /* H = demagnetisation field of m (Eq. 4), both device [3][nz][ny][nx]. */
 int mm_demag_field(mm_ctx* ctx, const void* m, void* H);
 

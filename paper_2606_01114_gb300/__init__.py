@@ -99,6 +99,7 @@ def _load():
                               ctypes.POINTER(ctypes.c_float)]),
         "mm_fno_set_output_scale": (I, [P, D]),
         "mm_set_dmi": (I, [P, D, I]),
+        "mm_set_stt": (I, [P, D, D, D, D, P, D]),
         "mm_minimize_bb": (I, [P, P, D, L, LP]),
         "mm_relax_surrogate": (I, [P, P, P, D, D, L, I, D, D, DP, LP, LP]),
     }
@@ -200,6 +201,11 @@ def mm_set_external_field(ctx, hx, hy, hz):
 
 def mm_set_dmi(ctx, D, kind=MM_DMI_INTERFACIAL):
     _check(ctx, _load().mm_set_dmi(ctx.handle, float(D), int(kind)))
+
+
+def mm_set_stt(ctx, J, P, Lambda, eps_prime, p, d=0.0):
+    pp = (ctypes.c_double * 3)(*[float(v) for v in p])
+    _check(ctx, _load().mm_set_stt(ctx.handle, float(J), float(P), float(Lambda), float(eps_prime), pp, float(d)))
 
 
 def mm_demag_field(ctx, m, H):

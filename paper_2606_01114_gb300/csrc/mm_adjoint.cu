@@ -328,7 +328,7 @@ int mm_rk4_step_vjp(mm_ctx* ctx, const void* m0, double dt, void* lam, void* gMs
     if (!ctx) return fail(nullptr, MM_ERR_INVALID_ARG, "ctx is NULL");
     if (!m0 || !lam || !gMs) return fail(ctx, MM_ERR_INVALID_ARG, "m0, lam and gMs must be device pointers");
     if (!(std::isfinite(dt) && dt > 0)) return fail(ctx, MM_ERR_INVALID_ARG, "dt must be > 0");
-    if (ctx->D != 0.0) return fail(ctx, MM_ERR_INVALID_ARG, "the adjoint does not cover DMI");
+    if (ctx->D != 0.0 || ctx->stt_on) return fail(ctx, MM_ERR_INVALID_ARG, "the adjoint covers neither DMI nor STT");
     MM_BIND(ctx);
     if (ctx->prec == MM_F64) return step_vjp<double>(ctx, (const double*)m0, dt, (double*)lam, (double*)gMs);
     return step_vjp<float>(ctx, (const float*)m0, dt, (float*)lam, (float*)gMs);
@@ -369,7 +369,7 @@ int mm_rk4_trajectory_vjp(mm_ctx* ctx, const void* m0, double dt, long nsteps, v
     if (!ctx) return fail(nullptr, MM_ERR_INVALID_ARG, "ctx is NULL");
     if (!m0 || !lam || !gMs || nsteps < 0 || !(std::isfinite(dt) && dt > 0))
         return fail(ctx, MM_ERR_INVALID_ARG, "device pointers, dt > 0 and nsteps >= 0 required");
-    if (ctx->D != 0.0) return fail(ctx, MM_ERR_INVALID_ARG, "the adjoint does not cover DMI");
+    if (ctx->D != 0.0 || ctx->stt_on) return fail(ctx, MM_ERR_INVALID_ARG, "the adjoint covers neither DMI nor STT");
     MM_BIND(ctx);
     if (nsteps == 0) return MM_OK;
     long K = checkpoint_every > 0 ? checkpoint_every : (long)std::ceil(std::sqrt((double)nsteps));

@@ -456,6 +456,27 @@ int mm_set_dmi(mm_ctx* ctx, double D, int type) {
     return MM_OK;
 }
 
+int mm_set_stt(mm_ctx* ctx, double J, double P, double Lambda, double eps_prime, const double p[3], double d) {
+    if (!ctx) return fail(nullptr, MM_ERR_INVALID_ARG, "ctx is NULL");
+    if (J == 0.0) {
+        ctx->stt_on = 0;
+        return MM_OK;
+    }
+    if (!p || !std::isfinite(J) || !std::isfinite(P) || !(Lambda >= 1.0) || !std::isfinite(eps_prime) ||
+        !std::isfinite(d))
+        return fail(ctx, MM_ERR_INVALID_ARG, "STT: finite J, P, eps', Lambda >= 1 and a polarisation vector required");
+    const double n = std::sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+    if (!(n > 0) || !std::isfinite(n)) return fail(ctx, MM_ERR_INVALID_ARG, "STT: polarisation vector must be non-zero");
+    ctx->stt_on = 1;
+    ctx->stt_J = J;
+    ctx->stt_P = P;
+    ctx->stt_L = Lambda;
+    ctx->stt_eps2 = eps_prime;
+    for (int c = 0; c < 3; ++c) ctx->stt_p[c] = p[c] / n;
+    ctx->stt_d = d > 0 ? d : ctx->nz * ctx->dz;
+    return MM_OK;
+}
+
 int mm_minimize_bb(mm_ctx* ctx, void* m, double torque_tol, long max_iter, long* iters_out) {
     if (!ctx) return fail(nullptr, MM_ERR_INVALID_ARG, "ctx is NULL");
     MM_BIND(ctx);

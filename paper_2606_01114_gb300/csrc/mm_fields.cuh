@@ -22,6 +22,10 @@ template <typename T> struct Params {
     T alpha;
     int dmi;            // 0 none, 1 interfacial, 2 bulk
     T dx_c, dy_c, dz_c; // D / (mu0 d) per axis
+    int stt;            // Slonczewski torque on
+    T stt_c;            // gamma hbar J / (mu0 e d (1 + alpha^2)); divided by Ms per cell
+    T stt_P, stt_L2, stt_eps2;
+    T px, py, pz;
 };
 
 template <typename T>
@@ -51,6 +55,14 @@ inline Params<T> make_params(const mm_ctx* ctx) {
     p.dx_c = (T)(ctx->D / (kMu0 * ctx->dx));
     p.dy_c = (T)(ctx->D / (kMu0 * ctx->dy));
     p.dz_c = (T)(ctx->D / (kMu0 * ctx->dz));
+    p.stt = ctx->stt_on;
+    p.stt_c = (T)(kGamma * kHbar * ctx->stt_J / (kMu0 * kQe * ctx->stt_d * (1.0 + ctx->alpha * ctx->alpha)));
+    p.stt_P = (T)ctx->stt_P;
+    p.stt_L2 = (T)(ctx->stt_L * ctx->stt_L);
+    p.stt_eps2 = (T)ctx->stt_eps2;
+    p.px = (T)ctx->stt_p[0];
+    p.py = (T)ctx->stt_p[1];
+    p.pz = (T)ctx->stt_p[2];
     return p;
 }
 
@@ -151,6 +163,24 @@ __device__ __forceinline__ V3<T> dmi_at(const Params<T>& p, const T* __restrict_
     }
     const T inv = (T)1 / Msi;
     return {hx * inv, hy * inv, hz * inv};
+}
+
+// Slonczewski spin-transfer torque (a local term beside Eq. 1; the form is
+// the reading taken): the Gilbert-form term gamma beta [eps m x (p x m) +
+// eps' p x m], beta = hbar J / (mu0 e Ms d), eps = P L^2 / ((L^2 + 1) +
+// (L^2 - 1) m.p), solved for dm/dt:
+//   gamma beta / (1 + alpha^2) [(eps + alpha eps') m x (p x m) - (eps' - alpha eps) m x p]
+template <typename T>
+__device__ __forceinline__ V3<T> stt_at(const Params<T>& p, V3<T> m, T Msi) {
+    const T mp = m.x * p.px + m.y * p.py + m.z * p.pz;
+    const T eps = p.stt_P * p.stt_L2 / ((p.stt_L2 + (T)1) + (p.stt_L2 - (T)1) * mp);
+    const T c = p.stt_c / Msi;
+    const T a = c * (eps + p.alpha * p.stt_eps2), b = c * (p.stt_eps2 - p.alpha * eps);
+    // m x (p x m) = (m.m) p - (m.p) m (stage states are not unit vectors);  m x p
+    const T mm = m.x * m.x + m.y * m.y + m.z * m.z;
+    const V3<T> dl = {mm * p.px - mp * m.x, mm * p.py - mp * m.y, mm * p.pz - mp * m.z};
+    const V3<T> mxp = {m.y * p.pz - m.z * p.py, m.z * p.px - m.x * p.pz, m.x * p.py - m.y * p.px};
+    return {a * dl.x - b * mxp.x, a * dl.y - b * mxp.y, a * dl.z - b * mxp.z};
 }
 
 template <typename T>

@@ -15,6 +15,8 @@ namespace mm {
 constexpr double kPi = 3.141592653589793238462643383279502884;
 constexpr double kMu0 = 4e-7 * kPi;
 constexpr double kGamma = 2.2127615e5;   // mu0 * gamma_e, m / (A s)
+constexpr double kHbar = 1.054571817e-34;   // J s
+constexpr double kQe = 1.602176634e-19;     // C
 
 // ---------------------------------------------------------------- complex
 template <typename T> struct cx;
@@ -81,6 +83,9 @@ struct mm_ctx {
     double Ms, A, alpha, Ku, u[3], hext[3];
     double D;                 // DMI constant (J/m^2)
     int dmi_type;             // 0 none, MM_DMI_INTERFACIAL, MM_DMI_BULK
+    // Slonczewski torque: on, J (A/m^2), P, Lambda, eps', unit p, free-layer thickness d (m)
+    int stt_on;
+    double stt_J, stt_P, stt_L, stt_eps2, stt_p[3], stt_d;
     bool has_Ms_cell, has_A_cell;
     void* Ms_cell;            // [N] path precision (allocated always; filled when used)
     void* A_cell;

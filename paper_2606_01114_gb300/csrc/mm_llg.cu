@@ -147,6 +147,10 @@ __global__ void k_stage(Params<T> p, const T* __restrict__ m_in, const T* __rest
                 h = {h.x + q.x, h.y + q.y, h.z + q.z};
             }
             ks = llg_rhs(p, mi, h);
+            if (p.stt) {
+                const V3<T> q = stt_at(p, mi, Msi);
+                ks = {ks.x + q.x, ks.y + q.y, ks.z + q.z};
+            }
         }
         V3<T> a0 = S == 0 ? mi : load3(m0, i, p.N);
         if constexpr (!LAST) {
@@ -592,7 +596,7 @@ template <typename T, int METHOD, int S>
 int launch_stage(mm_ctx* ctx, const Params<T>& p, const void* m_in, const void* m0, void* m_out, T* const* kdev) {
     KernelTimer kt(ctx, MM_K_STAGE);
     if constexpr (sizeof(T) == 4) {
-        if (!p.Ms_cell && !p.A_cell && p.Ms != 0.f && p.nx % 4 == 0 && !p.dmi) {
+        if (!p.Ms_cell && !p.A_cell && p.Ms != 0.f && p.nx % 4 == 0 && !p.dmi && !p.stt) {
             KPtrs kb;
             for (int s = 0; s < 6; ++s) kb.k[s] = (float*)ctx->k[s];
             const float inv = 1.f / p.Ms;
