@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=150.0, help="seconds of oracle work for the reference arm")
+    ap.add_argument("--ingest-ncu", metavar="CSV", default=None,
+                    help="write profiles/traffic.json from an ncu raw CSV export and exit")
     return ap.parse_args()
 
 
@@ -78,10 +80,22 @@ def load_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def source_hash():
+# the sources each timed kernel family is compiled from: stored ncu traffic
+# stays valid while these files are unchanged
+KERNEL_SOURCES = {
+    "demag": ("mm_demag.cu", "mm_fft.cuh", "mm_regfft.cuh", "mm_internal.cuh"),
+    "stage": ("mm_llg.cu", "mm_fields.cuh", "mm_internal.cuh"),
+}
+FAMILY = {"xfwd": "demag", "yfwd": "demag", "zconv": "demag", "yinv": "demag", "xinv": "demag", "stage": "stage"}
+# kernel-name prefixes of each timed class as ncu reports them
+NCU_NAMES = {"xfwd": "k_xfwd", "yfwd": "k_cols", "yinv": "k_cols", "zconv": "k_zconv", "xinv": "k_xinv",
+             "stage": "k_stage"}
+
+
+def source_hash(kernel):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2606_01114_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
+    for fn in KERNEL_SOURCES[FAMILY[kernel]]:
         with open(os.path.join(csrc, fn), "rb") as f:
             h.update(fn.encode())
             h.update(f.read())
@@ -90,7 +104,7 @@ def source_hash():
 
 def ncu_traffic(kernel, precision):
     """DRAM bytes per launch of ``kernel`` from the committed ncu summary, or
-    None when the kernel sources changed since the counters were taken."""
+    None when the kernel's sources changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -98,9 +112,52 @@ def ncu_traffic(kernel, precision):
     except Exception:
         return None
     e = t.get(f"{kernel}/{precision}")
-    if not e or e.get("source_sha") != source_hash():
+    if not e or e.get("source_sha") != source_hash(kernel):
         return None
     return float(e["bytes_per_launch"])
+
+
+def ingest_ncu(csv_path, precision, workload):
+    """Write profiles/traffic.json from an ncu raw CSV export
+    (``ncu -i rep --page raw --csv``): per timed kernel class, the
+    dram__bytes_read.sum + dram__bytes_write.sum of its first captured launch
+    (for the y passes, the forward launch is the one whose name carries
+    DIR = -1), stamped with the current source hash of its family."""
+    import csv
+    import re
+    with open(csv_path, newline="") as f:
+        rows = list(csv.reader(f))
+    head = rows[0]
+    col = {name: head.index(name) for name in ("Kernel Name", "dram__bytes_read.sum", "dram__bytes_write.sum")}
+    units = rows[1] if len(rows) > 1 and not rows[1][col["Kernel Name"]] else None
+    data = rows[2:] if units else rows[1:]
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+
+    def to_bytes(r, metric):
+        unit = units[col[metric]] if units else "byte"
+        return float(r[col[metric]].replace(",", "")) * scale.get(unit, 1)
+
+    out = {"_note": "DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu "
+                    "capture; valid while the kernel family's sources hash to source_sha"}
+    for k, prefix in NCU_NAMES.items():
+        for r in data:
+            mt = re.search(r"(k_\w+)<([^>]*)>", r[col["Kernel Name"]])
+            if not mt or not mt.group(1).startswith(prefix):
+                continue
+            if k in ("yfwd", "yinv"):
+                # k_cols_reg<L1, L2, DIR, PIN, POUT>: DIR is the third argument
+                direction = int(mt.group(2).split(",")[2].replace("(int)", "").strip())
+                if (direction < 0) != (k == "yfwd"):
+                    continue
+            rd, wr = to_bytes(r, "dram__bytes_read.sum"), to_bytes(r, "dram__bytes_write.sum")
+            out[f"{k}/{precision}"] = {"kernel": f"{mt.group(1)}<{mt.group(2)}>", "workload": workload,
+                                       "bytes_per_launch": int(rd + wr), "read": int(rd), "write": int(wr),
+                                       "source_sha": source_hash(k)}
+            break
+    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps(out, indent=1))
+    return 0
 
 
 class ClockSampler:
@@ -402,6 +459,8 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.ingest_ncu:
+        return ingest_ncu(args.ingest_ncu, args.precision, "film512 512x512x16 " + args.precision.upper())
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

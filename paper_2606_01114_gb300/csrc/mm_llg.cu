@@ -196,7 +196,7 @@ __global__ void k_stage(Params<T> p, const T* __restrict__ m_in, const T* __rest
             const bool bad = !(isfinite((double)mn.x) && isfinite((double)mn.y) && isfinite((double)mn.z));
             if (METHOD == MM_RKF45) {
                 // a trial that overflowed is rejected (infinite error), as any too-large step
-                err = (double)dt * sqrt((double)e.x * e.x + (double)e.y * e.y + (double)e.z * e.z);
+                err = (double)dt * (double)sqrt(e.x * e.x + e.y * e.y + e.z * e.z);
                 if (bad || !isfinite(err)) err = INFINITY;
             } else if (bad) {
                 atomicCAS(&ctl->status, 0, (int)MM_ERR_NONFINITE);
@@ -340,6 +340,7 @@ __global__ void __launch_bounds__(256) k_stage4(Params<float> p, float wx, float
             }
             Cells4 mo;
             bool bad = false;
+            float e2 = 0.f;   // max |m5 - m4|^2 / dt^2 of the quad, in the path's precision
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 float mx = at(a0.x, j) + dt * at(acc.x, j);
@@ -357,14 +358,15 @@ __global__ void __launch_bounds__(256) k_stage4(Params<float> p, float wx, float
                 at(mo.y, j) = my;
                 at(mo.z, j) = mz;
                 if (METHOD == MM_RKF45) {
-                    const double ej = (double)dt * sqrt((double)at(e.x, j) * at(e.x, j) +
-                                                        (double)at(e.y, j) * at(e.y, j) +
-                                                        (double)at(e.z, j) * at(e.z, j));
-                    err = fmax(err, isfinite(ej) ? ej : INFINITY);
+                    const float v = at(e.x, j) * at(e.x, j) + at(e.y, j) * at(e.y, j) + at(e.z, j) * at(e.z, j);
+                    bad |= !(v <= 3.0e38f);   // fmaxf would drop a NaN
+                    e2 = fmaxf(e2, v);
                 }
             }
             if (METHOD == MM_RKF45) {
-                if (bad) err = INFINITY;
+                // one square root per thread (FP64 arithmetic is slow on this part)
+                err = (double)dt * (double)sqrtf(e2);
+                if (bad || !isfinite(err)) err = INFINITY;
             } else if (bad) {
                 atomicCAS(&ctl->status, 0, (int)MM_ERR_NONFINITE);
             }
