@@ -28,7 +28,8 @@
  *   - Work is enqueued on the stream given at mm_init_mesh (or mm_set_stream).
  *     Calls that return host scalars (energies, torque, step errors) wait for
  *     that stream.  Calls on one context must not overlap on the host.
- *   - Mesh sizes: each of nx, ny, nz is 1 or a power of two up to 512.
+ *   - Mesh sizes: nx, ny any of 1..512 (powers of two take the radix-2 passes,
+ *     other sizes a direct O(n^2)-per-line DFT); nz 1 or a power of two up to 512.
  *   - Every function returns MM_OK (0) or a negative MM_ERR_* code;
  *     mm_last_error() then describes the failure.  A failed call leaves the
  *     caller's buffers in an unspecified state but the context usable, except

@@ -79,7 +79,10 @@ KernelTimer::~KernelTimer() {
 
 namespace {
 
-bool valid_n(int n) { return n >= 1 && n <= 512 && (n & (n - 1)) == 0; }
+// nx, ny: any size up to 512 (powers of two take the fast passes, other
+// sizes a direct DFT); nz: 1 or a power of two (the z pass is radix-2)
+bool valid_n(int n) { return n >= 1 && n <= 512; }
+bool valid_nz(int n) { return valid_n(n) && (n & (n - 1)) == 0; }
 bool valid_len(double d) { return std::isfinite(d) && d > 0.0; }
 
 size_t elem(const mm_ctx* ctx) { return ctx->prec == MM_F64 ? sizeof(double) : sizeof(float); }
@@ -220,9 +223,9 @@ int mm_init_mesh(mm_ctx** out, int nx, int ny, int nz, double dx, double dy, dou
                  void* stream) {
     if (!out) return fail(nullptr, MM_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
-    if (!valid_n(nx) || !valid_n(ny) || !valid_n(nz))
-        return fail(nullptr, MM_ERR_INVALID_ARG, "mesh %dx%dx%d: each size must be 1 or a power of two <= 512", nx, ny,
-                    nz);
+    if (!valid_n(nx) || !valid_n(ny) || !valid_nz(nz))
+        return fail(nullptr, MM_ERR_INVALID_ARG,
+                    "mesh %dx%dx%d: nx, ny in 1..512, nz 1 or a power of two <= 512", nx, ny, nz);
     if (!valid_len(dx) || !valid_len(dy) || !valid_len(dz))
         return fail(nullptr, MM_ERR_INVALID_ARG, "cell size must be finite and > 0");
     if (precision != MM_F32 && precision != MM_F64) return fail(nullptr, MM_ERR_INVALID_ARG, "bad precision");

@@ -291,6 +291,84 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512)
                      cstride, twz);
 }
 
+// ------------------------------------------------ direct DFT passes
+// Transform lengths that are not powers of two (meshes such as 100 x 25)
+// take these O(L^2)-per-line kernels: every output is the plain sum of its
+// DFT definition, one thread per output, twiddles from the length's table
+// (index (n k) mod L, advanced additively).  A correctness path beside the
+// power-of-two passes, not a fast one.
+inline bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// K2: X_k = sum_{x < nin} M_x exp(-2 pi i k x / Px), k = 0 .. Hx - 1
+template <typename T>
+__global__ void k_xfwd_direct(const T* __restrict__ in, long in_ld, int nin, const T* __restrict__ Ms, T ms,
+                              long ms_rows, C_t<T>* __restrict__ out, int Hs, int Hx, int Px, long rows,
+                              const C_t<T>* __restrict__ twP) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * Hx) return;
+    const long r = idx / Hx;
+    const int k = (int)(idx % Hx);
+    const T* row = in + r * in_ld;
+    const T* mrow = Ms ? Ms + (r % ms_rows) * in_ld : nullptr;
+    T re = 0, im = 0;
+    int m = 0;
+    for (int x = 0; x < nin; ++x) {
+        const T v = row[x] * (mrow ? mrow[x] : ms);
+        const C_t<T> w = twP[m];
+        re += v * w.x;
+        im += v * w.y;
+        m += k;
+        if (m >= Px) m -= Px;
+    }
+    out[r * Hs + k] = cmk<C_t<T>>(re, im);
+}
+
+// K6: out_x = scale / 2 [X_0 + (-1)^x X_nx + 2 sum_{k=1}^{nx-1} Re(X_k exp(+2 pi i k x / Px))]
+// (the full inverse over Px of a Hermitian spectrum; scale = 1 / (nx Py Pz))
+template <typename T>
+__global__ void k_xinv_direct(const C_t<T>* __restrict__ in, int Hs, T* __restrict__ out, int nx, int Px, long rows,
+                              T scale, const C_t<T>* __restrict__ twP) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * nx) return;
+    const long r = idx / nx;
+    const int x = (int)(idx % nx);
+    const C_t<T>* row = in + r * Hs;
+    T acc = 0;
+    int m = x;
+    for (int k = 1; k < nx; ++k) {
+        const C_t<T> w = twP[m];                      // exp(-i theta); the conjugate is exp(+i theta)
+        acc += row[k].x * w.x + row[k].y * w.y;       // Re(X_k conj(w))
+        m += x;
+        if (m >= Px) m -= Px;
+    }
+    const T nyq = (x & 1) ? -row[nx].x : row[nx].x;
+    out[r * (long)nx + x] = (T)0.5 * scale * (row[0].x + nyq + (T)2 * acc);
+}
+
+// K3 / K5 along a strided axis: out[k] = sum_{n < nin} in[n] exp(DIR 2 pi i n k / L), k < nout
+template <typename T, int DIR>
+__global__ void k_cols_direct(const C_t<T>* __restrict__ in, C_t<T>* __restrict__ out, int L, int nin, int nout,
+                              int Hx, ColGeom cg, const C_t<T>* __restrict__ tw) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = blockIdx.y;
+    if (idx >= (long)nout * Hx) return;
+    const int k = (int)(idx / Hx), col = (int)(idx % Hx);
+    const int pi = p % cg.n_inner, po = p / cg.n_inner;
+    const C_t<T>* ib = in + pi * cg.in_inner + po * cg.in_outer + col;
+    T re = 0, im = 0;
+    int m = 0;
+    for (int n = 0; n < nin; ++n) {
+        const C_t<T> v = ib[(long)n * cg.rs_in];
+        C_t<T> w = tw[m];
+        if (DIR > 0) w.y = -w.y;
+        re += v.x * w.x - v.y * w.y;
+        im += v.x * w.y + v.y * w.x;
+        m += k;
+        if (m >= L) m -= L;
+    }
+    out[pi * cg.out_inner + po * cg.out_outer + (long)k * cg.rs_out + col] = cmk<C_t<T>>(re, im);
+}
+
 // ------------------------------------------- FP32 register-resident passes
 // K4 for Pz <= 32: one thread per (component, column) holds its whole z line
 // in registers; forward DFT (upper half zero), the 3x3 product through shared
@@ -661,6 +739,14 @@ int try_xinv_reg(mm_ctx* ctx, const float2* in, float* out, long rows, float sca
 template <typename T>
 int run_xfwd(mm_ctx* ctx, const T* in, long in_ld, int nin, const T* Ms, T ms, long ms_rows, C_t<T>* out,
              long rows, const C_t<T>* twL, const C_t<T>* twP, int Px) {
+    if (!pow2(Px)) {
+        KernelTimer kt(ctx, MM_K_XFWD);
+        const long n = rows * ctx->Hx;
+        k_xfwd_direct<T><<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(in, in_ld, nin, Ms, ms, ms_rows, out,
+                                                                               ctx->Hs, ctx->Hx, Px, rows, twP);
+        MM_LAUNCH_CHECK(ctx);
+        return MM_OK;
+    }
     KernelTimer kt(ctx, MM_K_XFWD);
     if (Px == 1) {
         k_x1fwd<T><<<(unsigned)((rows + 255) / 256), 256, 0, ctx->stream>>>(in, Ms, ms, ms_rows, out, ctx->Hs, rows);
@@ -720,6 +806,13 @@ template <typename T, int DIR>
 int run_cols(mm_ctx* ctx, const C_t<T>* in, C_t<T>* out, int L, int nin, int nout, int nplanes, ColGeom g,
              const C_t<T>* tw) {
     KernelTimer kt(ctx, DIR < 0 ? MM_K_YFWD : MM_K_YINV);
+    if (!pow2(L)) {
+        if ((const void*)in == (const void*)out) return fail(ctx, MM_ERR_INVALID_ARG, "direct DFT pass needs out != in");
+        dim3 grid((unsigned)(((long)nout * ctx->Hx + 255) / 256), (unsigned)nplanes);
+        k_cols_direct<T, DIR><<<grid, 256, 0, ctx->stream>>>(in, out, L, nin, nout, ctx->Hx, g, tw);
+        MM_LAUNCH_CHECK(ctx);
+        return MM_OK;
+    }
     if constexpr (sizeof(T) == 4) {
         const bool product_pruning = DIR < 0 ? (nin == L / 2 && nout == L) : (nin == L && nout == L / 2);
         if (product_pruning && ctx->fft_mode != 0 && (L == 512 || L == 1024))
@@ -826,6 +919,13 @@ int xinv_pass(mm_ctx* ctx, const C_t<T>* xin, T* H, long rows) {
     int rc;
     const T scale = (T)(1.0 / ((double)ctx->Lx * ctx->Py * ctx->Pz));
     KernelTimer kt(ctx, MM_K_XINV);
+    if (!pow2(ctx->Px)) {
+        const long n = rows * ctx->nx;
+        k_xinv_direct<T><<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(
+            xin, ctx->Hs, H, ctx->nx, ctx->Px, rows, scale, table<T>(ctx, ctx->tw.off_px));
+        MM_LAUNCH_CHECK(ctx);
+        return MM_OK;
+    }
     if (ctx->Px == 1) {
         k_x1inv<T><<<(unsigned)((rows + 255) / 256), 256, 0, ctx->stream>>>(xin, ctx->Hs, H, rows, scale);
         MM_LAUNCH_CHECK(ctx);
@@ -861,15 +961,18 @@ int setup(mm_ctx* ctx) {
     double2* X = nullptr;
     double2* fg = nullptr;
     double* oct = nullptr;
+    double2* X2 = nullptr;   // out-of-place target of a direct (non-power-of-two) y transform
     int rc = MM_OK;
     auto cleanup = [&]() {
         cudaFree(grid);
         cudaFree(X);
         cudaFree(fg);
         cudaFree(oct);
+        cudaFree(X2);
     };
     if (cudaMalloc(&grid, sizeof(double) * gsize) != cudaSuccess || cudaMalloc(&X, sizeof(double2) * csize) != cudaSuccess ||
-        cudaMalloc(&fg, sizeof(double2) * fsize) != cudaSuccess || cudaMalloc(&oct, sizeof(double) * 6 * ctx->N) != cudaSuccess) {
+        cudaMalloc(&fg, sizeof(double2) * fsize) != cudaSuccess || cudaMalloc(&oct, sizeof(double) * 6 * ctx->N) != cudaSuccess ||
+        (!pow2(ctx->Py) && cudaMalloc(&X2, sizeof(double2) * csize) != cudaSuccess)) {
         cleanup();
         cudaGetLastError();
         return fail(ctx, MM_ERR_NOMEM, "device allocation for the Newell setup failed");
@@ -882,19 +985,21 @@ int setup(mm_ctx* ctx) {
         if (rc) break;
         rc = run_xfwd<double>(ctx, grid, ctx->Px, ctx->Px, nullptr, 1.0, 1, X, (long)ctx->Pz * ctx->Py, twL, twP, ctx->Px);
         if (rc) break;
+        double2* Y = X;   // the spectrum after the y transform
         if (ctx->Py > 1) {
             ColGeom g{ctx->Hs, ctx->Hs, ctx->Pz, (long)ctx->Py * ctx->Hs, 0, (long)ctx->Py * ctx->Hs, 0};
-            rc = run_cols<double, -1>(ctx, X, X, ctx->Py, ctx->Py, ctx->Py, ctx->Pz, g, table<double>(ctx, ctx->tw.off_py));
+            if (X2) Y = X2;
+            rc = run_cols<double, -1>(ctx, X, Y, ctx->Py, ctx->Py, ctx->Py, ctx->Pz, g, table<double>(ctx, ctx->tw.off_py));
             if (rc) break;
         }
         if (ctx->Pz > 1) {
             long rs = (long)ctx->Py * ctx->Hs;
             ColGeom g{rs, rs, ctx->Py, ctx->Hs, 0, ctx->Hs, 0};
-            rc = run_cols<double, -1>(ctx, X, X, ctx->Pz, ctx->Pz, ctx->Pz, ctx->Py, g, table<double>(ctx, ctx->tw.off_pz));
+            rc = run_cols<double, -1>(ctx, Y, Y, ctx->Pz, ctx->Pz, ctx->Pz, ctx->Py, g, table<double>(ctx, ctx->tw.off_pz));
             if (rc) break;
         }
         long total = kcomp;
-        k_extract<T><<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(X, ctx->Py, ctx->Hs, ctx->Hx, ctx->Py2,
+        k_extract<T><<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(Y, ctx->Py, ctx->Hs, ctx->Hx, ctx->Py2,
                                                                                ctx->Pz2, (T*)ctx->kern + c * kcomp);
         ctx->launches++;
         if (cudaGetLastError() != cudaSuccess) {
