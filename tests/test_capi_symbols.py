@@ -47,7 +47,7 @@ def test_python_binding_has_the_same_names(lib):
         assert callable(getattr(mm, name)), name
 
 
-@pytest.mark.parametrize("n", [(5, 4, 4), (4, 0, 4), (1024, 4, 4), (4, 4, 3)])
+@pytest.mark.parametrize("n", [(4, 4, 6), (4, 0, 4), (1024, 4, 4), (4, 4, 3), (513, 8, 1)])
 def test_invalid_mesh_rejected_without_device_work(lib, n):
     with pytest.raises(mm.MMError) as e:
         mm.mm_init_mesh(*n, 1e-9, 1e-9, 1e-9)
