@@ -475,6 +475,17 @@ def mm_relax_surrogate(ctx, f, m, t_max, torque_tol=1e-4, max_steps=1000000, k_e
     return tt.value, ss.value, st[0], st[1], st[2]
 
 
+def relax(ctx, m, t_max, torque_tol=1e-4, max_steps=1000000, surrogate=None, k=10, bound=1e-3, torque_exact=1e-2):
+    """relax() of m in place: RKF45 until max |m x H_eff| / Ms <= torque_tol or
+    t_max (mm_relax), or with a trained surrogate for the demag field in the
+    stages (mm_relax_surrogate: exact field and residual check every k
+    steps, exact final approach below torque_exact).  Returns (t, steps)."""
+    if surrogate is None:
+        return mm_relax(ctx, m, t_max, torque_tol, max_steps)
+    t, steps, _, _, _ = mm_relax_surrogate(ctx, surrogate, m, t_max, torque_tol, max_steps, k, bound, torque_exact)
+    return t, steps
+
+
 def from_paper_layout(m_xyz3):
     """(nx, ny, nz, 3) -> (3, nz, ny, nx), the library's component-planar layout."""
     return m_xyz3.permute(3, 2, 1, 0).contiguous() if hasattr(m_xyz3, "permute") else \

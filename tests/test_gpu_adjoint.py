@@ -224,3 +224,22 @@ def test_checkpoint_interval_does_not_change_the_gradient():
     for o in out[1:]:
         np.testing.assert_allclose(o, out[0], rtol=1e-12, atol=1e-30)
     mm.mm_destroy(ctx)
+
+
+def test_llg_step_autograd_against_central_differences():
+    from paper_2606_01114_gb300.autograd import LLGStep
+    Ms = wl.smooth_field(N_SMALL, 4e5, 9e5, sigma_cells=2.0, seed=12)
+    ctx = make_ctx(N_SMALL, D_SMALL, Ms, Ku=1e5, u=(0.0, 0.6, 0.8), alpha=0.05)
+    rng = np.random.default_rng(13)
+    m0 = dev(wl.random_unit(N_SMALL, seed=14)).requires_grad_(True)
+    Ms_t = dev(Ms).requires_grad_(True)
+    w = dev(rng.standard_normal(ctx.shape3))
+    L = torch.sum(w * LLGStep.apply(m0, Ms_t, ctx, 5e-14))
+    L.backward()
+    v = dev(rng.standard_normal(ctx.shape3))
+
+    def f(e):
+        with torch.no_grad():
+            return float(torch.sum(w * LLGStep.apply(m0.detach() + e * v, Ms_t.detach(), ctx, 5e-14)))
+    assert richardson(f, 1e-4) == pytest.approx(vdot(m0.grad, v), rel=1e-7)
+    mm.mm_destroy(ctx)

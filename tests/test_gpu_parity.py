@@ -240,6 +240,31 @@ def test_rkf45_rejects_then_accepts_fp64():
     mm.mm_destroy(ctx)
 
 
+@pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
+def test_rkf45_trajectory_replayed_by_the_oracle(prec):
+    """Adaptive RKF45 on the GPU for 40 accepted steps; the oracle replays
+    the GPU's accepted step sizes (rkf45_trial with each dt) and the states
+    agree step by step, while every proposed next step follows the
+    controller formula from the GPU's own error."""
+    n, d = (16, 16, 2), (2.5e-9, 2.5e-9, 3e-9)
+    p = micromag.Problem(n, d, alpha=0.1, Ku=2e5, u=(0, 0, 1), h_ext=(2e4, 0, 0))
+    m = wl.random_unit(n, seed=21)
+    ctx = gpu_ctx(p, prec)
+    md = dev(m, prec)
+    t, dt = 0.0, 1e-14
+    worst = 0.0
+    for _ in range(40):
+        t_new, dt_next, err = mm.mm_llg_step(ctx, md, t, dt, mm.MM_RKF45, tol=1e-5)
+        h = t_new - t
+        m, err_o = p.rkf45_trial(m, h)
+        worst = max(worst, rel_l2(host(md), m))
+        assert err <= 1e-5
+        assert dt_next == pytest.approx(micromag.next_dt(h, err, 1e-5), rel=1e-9)
+        t, dt = t_new, dt_next
+    assert worst < (1e-12 if prec == mm.MM_F64 else 2e-5), worst
+    mm.mm_destroy(ctx)
+
+
 def test_relax_macrospin_aligns_with_field():
     p = micromag.Problem((1, 1, 1), (2e-9, 2e-9, 2e-9), alpha=0.5, h_ext=(0, 0, 3e5))
     m = np.array([np.sin(1.0) * np.cos(0.3), np.sin(1.0) * np.sin(0.3), np.cos(1.0)]).reshape(3, 1, 1, 1)
