@@ -323,7 +323,8 @@ int mm_fno_set_output_scale(mm_fno* f, double scale);
  * MM_F32 context, nz = 1, uniform Ms, surrogate of the same grid (its
  * launches go to the context's stream for the call).  stats (nullable, 3
  * longs): exact demag evaluations, surrogate evaluations, failed checks.
- * Not thread-safe: one call at a time per process. */
+ * One call at a time per surrogate: the call sets the surrogate's stream
+ * and output scale for its duration. */
 int mm_relax_surrogate(mm_ctx* ctx, mm_fno* f, void* m, double t_max, double torque_tol, long max_steps,
                        int k_exact, double bound, double torque_exact, double* t_out, long* steps_out, long* stats);
 

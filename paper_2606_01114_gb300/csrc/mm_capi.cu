@@ -168,15 +168,12 @@ void reset_ctl(Control* c, double t, double dt, double t_max, double tol) {
 
 // demag field of a stage state: the exact convolution, or the surrogate
 // (output scaled by Ms) when one is attached for this window
-mm_fno* g_stage_surrogate = nullptr;
-long g_surrogate_evals = 0, g_exact_evals = 0;
-
 int stage_field(mm_ctx* ctx, const void* m_in) {
-    if (g_stage_surrogate) {
-        ++g_surrogate_evals;
-        return mm_fno_forward(g_stage_surrogate, m_in, ctx->Hd, 1);
+    if (ctx->stage_surrogate) {
+        ++ctx->surrogate_evals;
+        return mm_fno_forward(ctx->stage_surrogate, m_in, ctx->Hd, 1);
     }
-    ++g_exact_evals;
+    ++ctx->exact_evals;
     return demag_apply(ctx, m_in, ctx->Hd);
 }
 
@@ -531,7 +528,7 @@ int mm_relax_surrogate(mm_ctx* ctx, mm_fno* f, void* m, double t_max, double tor
     reset_ctl(ctx->ctl_host, 0.0, std::fmin(1e-14, t_max), t_max, 1e-5);
     if ((rc = push_ctl(ctx))) return rc;
     if ((rc = check_finite_launch(ctx, m))) return rc;
-    long exact0 = g_exact_evals, sur0 = g_surrogate_evals, fallbacks = 0, attempts = 0;
+    long exact0 = ctx->exact_evals, sur0 = ctx->surrogate_evals, fallbacks = 0, attempts = 0;
     const long max_attempts = 20 * (max_steps + 10);
     // after a failed residual check the next check waits 1, 2, 4, ... windows
     // (at most 64), so a surrogate that does not fit the state costs little
@@ -540,7 +537,7 @@ int mm_relax_surrogate(mm_ctx* ctx, mm_fno* f, void* m, double t_max, double tor
     while (rc == MM_OK) {
         // window start: exact field and torque, then (when due) the surrogate's residual
         MM_CUDA_CHECK(ctx, cudaMemsetAsync(&ctx->ctl->torque_bits, 0, sizeof(unsigned long long), ctx->stream));
-        ++g_exact_evals;
+        ++ctx->exact_evals;
         if ((rc = demag_apply(ctx, m, ctx->Hs_field))) break;
         if ((rc = torque_launch(ctx, m, ctx->Hs_field))) break;
         if ((rc = pull_ctl(ctx))) break;
@@ -563,7 +560,7 @@ int mm_relax_surrogate(mm_ctx* ctx, mm_fno* f, void* m, double t_max, double tor
             if (skip > 0) {
                 --skip;
             } else {
-                ++g_surrogate_evals;
+                ++ctx->surrogate_evals;
                 if ((rc = mm_fno_forward(f, m, ctx->Hd, 1))) break;
                 double loss = 0.0;
                 if ((rc = mm_fno_loss(f, ctx->Hd, ctx->Hs_field, nullptr, 1, &loss))) break;
@@ -577,7 +574,7 @@ int mm_relax_surrogate(mm_ctx* ctx, mm_fno* f, void* m, double t_max, double tor
                 }
             }
         }
-        g_stage_surrogate = use ? f : nullptr;
+        ctx->stage_surrogate = use ? f : nullptr;
         const long target = steps_now + k_exact;
         for (int k = 0; k < 4 * k_exact && rc == MM_OK; ++k, ++attempts) {
             rc = trial(ctx, m, MM_RKF45);
@@ -586,14 +583,14 @@ int mm_relax_surrogate(mm_ctx* ctx, mm_fno* f, void* m, double t_max, double tor
                 if (ctx->ctl_host->steps >= target || ctx->ctl_host->done || ctx->ctl_host->status) break;
             }
         }
-        g_stage_surrogate = nullptr;
+        ctx->stage_surrogate = nullptr;
     }
-    g_stage_surrogate = nullptr;
+    ctx->stage_surrogate = nullptr;
     fno_swap_stream(f, fno_stream);
     mm_fno_set_output_scale(f, 1.0);
     if (stats) {
-        stats[0] = g_exact_evals - exact0;
-        stats[1] = g_surrogate_evals - sur0;
+        stats[0] = ctx->exact_evals - exact0;
+        stats[1] = ctx->surrogate_evals - sur0;
         stats[2] = fallbacks;
     }
     return rc;

@@ -78,6 +78,8 @@ struct mm_ctx {
     int Hs;                   // row stride of k-space arrays (Hx rounded up to 16)
     int Py2, Pz2;             // Py/2+1, Pz/2+1: stored kernel octant extents
     int fft_mode;             // 0 plain FP32 passes, MM_TC_TF32 / MM_TC_BF16: tensor-core y passes
+    mm_fno* stage_surrogate;  // set inside mm_relax_surrogate while a window uses the surrogate
+    long surrogate_evals, exact_evals;   // demag evaluations of either kind (surrogate relax statistics)
 
     // material
     double Ms, A, alpha, Ku, u[3], hext[3];
