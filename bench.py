@@ -118,11 +118,12 @@ def ncu_traffic(kernel, precision):
 
 
 def ingest_ncu(csv_path, precision, workload):
-    """Write profiles/traffic.json from an ncu raw CSV export
-    (``ncu -i rep --page raw --csv``): per timed kernel class, the
-    dram__bytes_read.sum + dram__bytes_write.sum of its first captured launch
-    (for the y passes, the forward launch is the one whose name carries
-    DIR = -1), stamped with the current source hash of its family."""
+    """Update profiles/traffic.json from an ncu raw CSV export
+    (``ncu -i rep --page raw --csv``): per timed kernel class found in the
+    capture, the dram__bytes_read.sum + dram__bytes_write.sum of its first
+    captured launch (for the y passes, the forward launch is the one whose
+    name carries DIR = -1), stamped with the current source hash of its
+    family; classes not in the capture keep their entries."""
     import csv
     import re
     with open(csv_path, newline="") as f:
@@ -137,8 +138,14 @@ def ingest_ncu(csv_path, precision, workload):
         unit = units[col[metric]] if units else "byte"
         return float(r[col[metric]].replace(",", "")) * scale.get(unit, 1)
 
-    out = {"_note": "DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu "
-                    "capture; valid while the kernel family's sources hash to source_sha"}
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            out = json.load(f)          # kernels absent from this capture keep their entries
+    except Exception:
+        out = {}
+    out["_note"] = ("DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an ncu "
+                    "capture; valid while the kernel family's sources hash to source_sha")
     for k, prefix in NCU_NAMES.items():
         for r in data:
             mt = re.search(r"(k_\w+)<([^>]*)>", r[col["Kernel Name"]])
@@ -154,7 +161,7 @@ def ingest_ncu(csv_path, precision, workload):
                                        "bytes_per_launch": int(rd + wr), "read": int(rd), "write": int(wr),
                                        "source_sha": source_hash(k)}
             break
-    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
+    with open(path, "w") as f:
         json.dump(out, f, indent=1)
     print(json.dumps(out, indent=1))
     return 0
