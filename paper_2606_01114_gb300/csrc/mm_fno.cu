@@ -49,6 +49,7 @@ struct mm_fno {
     void* dv;           // [2][B][W][P]    ping-pong cotangents (FP32)
     float2* twx;        // [M][NX]  e^{-2 pi i kx x / NX}
     float2* twy;        // [MY][NY] e^{-2 pi i ky y / NY}
+    float* basis;       // [2M][NX] inverse-x basis c_kx (cos, -sin) / (NX NY), c_0 = 1, else 2
     double* red;        // loss reduction scratch [2][B]
     float out_scale;    // multiply h by this on output (Ms inside relax)
     std::string err;
@@ -84,32 +85,73 @@ __global__ void k_chan(const SI* __restrict__ X, const float* __restrict__ Wt, c
     if (idx >= (long)B * P) return;
     const int b = (int)(idx / P);
     const long p = idx % P;
-    float x[32];
-    for (int ci = 0; ci < Ci; ++ci) x[ci] = ld(X, ((long)b * Ci + ci) * P + p);
+    float x[32];   // unrolled to the maximum width so that it stays in registers
+#pragma unroll
+    for (int ci = 0; ci < 32; ++ci) x[ci] = ci < Ci ? ld(X, ((long)b * Ci + ci) * P + p) : 0.f;
     for (int co = 0; co < Co; ++co) {
         float acc = bias ? bias[co] : 0.f;
-        for (int ci = 0; ci < Ci; ++ci) acc += (transpose ? Wt[ci * Co + co] : Wt[co * Ci + ci]) * x[ci];
+#pragma unroll
+        for (int ci = 0; ci < 32; ++ci)
+            if (ci < Ci) acc += (transpose ? Wt[ci * Co + co] : Wt[co * Ci + ci]) * x[ci];
         st(Y, ((long)b * Co + co) * P + p, acc * scale);
     }
 }
 
-// A[row][kx] = sum_x X[row][x] e^{-2 pi i kx x / NX} * colscale(kx); rows = B W NY
+// A[row][kx] = sum_x X[row][x] e^{-2 pi i kx x / NX} * colscale(kx); rows = B W NY.
+// A GEMM of the rows against the twiddle table: 64 rows per block, x in
+// chunks of 32 staged in shared memory with the matching twiddles; thread t
+// owns row t / 4 and the modes kx = t % 4 + 4 j (M <= 32).
+constexpr int kDxRows = 64, kDxChunk = 32, kMaxModes = 32;
+
 template <typename SI>
-__global__ void k_dft_x(const SI* __restrict__ X, float2* __restrict__ A, const float2* __restrict__ twx, long rows,
-                        int NX, int M, float scale0, float scale1) {
-    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= rows * M) return;
-    const long row = idx / M;
-    const int kx = (int)(idx % M);
-    float re = 0.f, im = 0.f;
-    for (int x = 0; x < NX; ++x) {
-        const float v = ld(X, row * NX + x);
-        const float2 w = twx[kx * NX + x];
-        re += v * w.x;
-        im += v * w.y;
+__global__ void __launch_bounds__(256) k_dft_x(const SI* __restrict__ X, float2* __restrict__ A,
+                                               const float2* __restrict__ twx, long rows, int NX, int M, float scale0,
+                                               float scale1) {
+    __shared__ float xs[kDxRows][kDxChunk + 1];
+    __shared__ float2 ts[kDxChunk][kMaxModes];
+    const int tid = threadIdx.x;
+    const long r0 = (long)blockIdx.x * kDxRows;
+    const int rl = tid >> 2, g = tid & 3;
+    float2 acc[kMaxModes / 4];
+#pragma unroll
+    for (int j = 0; j < kMaxModes / 4; ++j) acc[j] = make_float2(0.f, 0.f);
+    for (int x0 = 0; x0 < NX; x0 += kDxChunk) {
+        for (int e = tid; e < kDxRows * kDxChunk; e += blockDim.x) {
+            const int r = e / kDxChunk, x = e % kDxChunk;
+            const long row = r0 + r;
+            xs[r][x] = (row < rows && x0 + x < NX) ? ld(X, row * NX + x0 + x) : 0.f;
+        }
+        for (int e = tid; e < M * kDxChunk; e += blockDim.x) {
+            const int k = e / kDxChunk, x = e % kDxChunk;
+            ts[x][k] = x0 + x < NX ? twx[(long)k * NX + x0 + x] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int x = 0; x < kDxChunk; ++x) {
+            const float v = xs[rl][x];
+#pragma unroll
+            for (int j = 0; j < kMaxModes / 4; ++j) {
+                const int k = g + 4 * j;
+                if (k < M) {
+                    const float2 w = ts[x][k];
+                    acc[j].x += v * w.x;
+                    acc[j].y += v * w.y;
+                }
+            }
+        }
+        __syncthreads();
     }
-    const float s = kx == 0 ? scale0 : scale1;
-    A[idx] = make_float2(re * s, im * s);
+    const long row = r0 + rl;
+    if (row < rows) {
+#pragma unroll
+        for (int j = 0; j < kMaxModes / 4; ++j) {
+            const int k = g + 4 * j;
+            if (k < M) {
+                const float sc = k == 0 ? scale0 : scale1;
+                A[row * M + k] = make_float2(acc[j].x * sc, acc[j].y * sc);
+            }
+        }
+    }
 }
 
 // along y between NY rows and the 2M retained rows; fwd: out[r] = sum_y in[y]
@@ -138,6 +180,37 @@ __global__ void k_dft_y(const float2* __restrict__ in, float2* __restrict__ out,
         im += v.x * w.y + v.y * w.x;
     }
     out[idx] = make_float2(re, im);
+}
+
+// NY -> 2M retained rows with the sum over y split over 8 lanes (shuffle
+// reduction): out[bw][r][kx] = sum_y in[bw][y][kx] e^{sign 2 pi i ky(r) y / NY}
+__global__ void k_dft_y_modes(const float2* __restrict__ in, float2* __restrict__ out,
+                              const float2* __restrict__ twy, int BW, int NY, int M, float sign) {
+    const int MY = 2 * M;
+    const long nout = (long)BW * MY * M;
+    const long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long idx = gid >> 3;
+    const int lane = (int)(gid & 7);
+    float re = 0.f, im = 0.f;
+    if (idx < nout) {
+        const int kx = (int)(idx % M);
+        const long rest = idx / M;
+        const int r = (int)(rest % MY);
+        const long bw = rest / MY;
+        for (int y = lane; y < NY; y += 8) {
+            float2 w = twy[(long)r * NY + y];     // e^{-2 pi i ky y / NY}
+            w.y *= -sign;
+            const float2 v = in[(bw * NY + y) * M + kx];
+            re += v.x * w.x - v.y * w.y;
+            im += v.x * w.y + v.y * w.x;
+        }
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (idx < nout && lane == 0) out[idx] = make_float2(re, im);
 }
 
 // T[b][co][k] = sum_ci R[co][ci][k] S[b][ci][k]; adjoint: S' = sum_co conj(R[co][ci]) T
@@ -178,36 +251,85 @@ __global__ void k_mix_grad(const float2* __restrict__ dT, const float2* __restri
     dR[idx].y += im;
 }
 
-// a[b][co][p] = W v + bias + IDFT_x(U)[co][y][x];  v_next = GELU(a) or a
+// a[b][co][p] = W v + bias + IDFT_x(U)[co][y][x];  v_next = GELU(a) or a.
+// Per (y, b) row and tile of 256 x, one GEMM with K = W + 2M:
+//   a[co][x] = bias[co] + sum_k Am[co][k] Bm[k][x],
+//   Am = [W | Re U, Im U],  Bm = [v rows ; basis rows],
+// the basis rows holding c_kx Re / Im of e^{-2 pi i kx x / NX} / (NX NY)
+// (Re(u conj(w)) = u.x w.x + u.y w.y).  Both operands in shared memory,
+// each thread an 8 (co) x 4 (x) register tile.
+constexpr int kLoTile = 256;
+
 template <typename SS>
-__global__ void k_layer_out(const SS* __restrict__ v, const float2* __restrict__ U, const float* __restrict__ Wt,
-                            const float* __restrict__ bias, const float2* __restrict__ twx, SS* __restrict__ a_out,
-                            SS* __restrict__ v_next, int B, int W, int NY, int NX, int M, int last) {
+__global__ void __launch_bounds__(256) k_layer_out(const SS* __restrict__ v, const float2* __restrict__ U,
+                                                   const float* __restrict__ Wt, const float* __restrict__ bias,
+                                                   const float* __restrict__ basis, SS* __restrict__ a_out,
+                                                   SS* __restrict__ v_next, int B, int W, int NY, int NX, int M,
+                                                   int last) {
+    constexpr int KMAX = 32 + 2 * kMaxModes;
+    __shared__ float As[32][KMAX + 1];
+    extern __shared__ __align__(16) float Bs[];           // [K][kLoTile]
+    const int y = blockIdx.x, b = blockIdx.y, x0 = blockIdx.z * kLoTile;
+    const int K = W + 2 * M;
     const long P = (long)NY * NX;
-    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long)B * P) return;
-    const int b = (int)(idx / P);
-    const long p = idx % P;
-    const int y = (int)(p / NX), x = (int)(p % NX);
-    float vin[32];
-    for (int ci = 0; ci < W; ++ci) vin[ci] = ld(v, ((long)b * W + ci) * P + p);
-    const float inv = 1.f / (float)P;
-    for (int co = 0; co < W; ++co) {
-        float acc = bias[co];
-        for (int ci = 0; ci < W; ++ci) acc += Wt[co * W + ci] * vin[ci];
-        const float2* u = U + (((long)b * W + co) * NY + y) * M;
-        float z = 0.f;
-        for (int kx = 0; kx < M; ++kx) {
-            const float2 w = twx[kx * NX + x];      // conj gives e^{+i theta}
-            const float re = u[kx].x * w.x + u[kx].y * w.y;
-            z += (kx == 0 ? 1.f : 2.f) * re;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < 32 * K; e += blockDim.x) {
+        const int co = e / K, k = e % K;
+        float val = 0.f;
+        if (co < W) {
+            if (k < W) {
+                val = Wt[co * W + k];
+            } else {
+                const int kx = (k - W) >> 1;
+                const float2 u = U[(((long)b * W + co) * NY + y) * M + kx];
+                val = ((k - W) & 1) ? u.y : u.x;
+            }
         }
-        acc += z * inv;
-        const long o = ((long)b * W + co) * P + p;
-        st(a_out, o, acc);
-        st(v_next, o, last ? acc : gelu(acc));
+        As[co][k] = val;
+    }
+    for (int e = tid; e < K * kLoTile; e += blockDim.x) {
+        const int k = e / kLoTile, x = e % kLoTile;
+        float val = 0.f;
+        if (x0 + x < NX)
+            val = k < W ? ld(v, ((long)b * W + k) * P + (long)y * NX + x0 + x) : basis[(long)(k - W) * NX + x0 + x];
+        Bs[k * kLoTile + x] = val;
+    }
+    __syncthreads();
+    const int cg = tid >> 6, xg = tid & 63;
+    float acc[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int k = 0; k < K; ++k) {
+        float av[8], bv[4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) av[i] = As[8 * cg + i][k];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bv[j] = Bs[k * kLoTile + xg + 64 * j];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int co = 8 * cg + i;
+        if (co >= W) continue;
+        const float bb = bias[co];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int x = x0 + xg + 64 * j;
+            if (x >= NX) continue;
+            const float val = acc[i][j] + bb;
+            const long o = ((long)b * W + co) * P + (long)y * NX + x;
+            st(a_out, o, val);
+            st(v_next, o, last ? val : gelu(val));
+        }
     }
 }
+
+inline size_t layer_out_smem(int W, int M) { return (size_t)(W + 2 * M) * kLoTile * sizeof(float); }
 
 // da = dvn * GELU'(a) (or dvn for the last layer), FP32 in place
 template <typename SS>
@@ -233,26 +355,65 @@ __global__ void k_dft_x_adj(const float2* __restrict__ dA, float* __restrict__ d
     dX[idx] = accumulate ? dX[idx] + s : s;
 }
 
-// dW[co][ci] += sum_{b,p} dY[b][co][p] X[b][ci][p]; db[co] += sum dY
+// dW[co][ci] += sum_{b,p} dY[b][co][p] X[b][ci][p]; db[co] += sum dY (the
+// column ci == Ci).  Blocks walk chunks of 128 pixels of one sample, stage
+// dY and X for the chunk in shared memory and accumulate their share of the
+// Co (Ci + 1) outputs in registers; one atomic add per output per block.
+constexpr int kWgChunk = 128;
+
 template <typename SX>
-__global__ void k_wgrad(const float* __restrict__ dY, const SX* __restrict__ X, float* __restrict__ dW,
-                        float* __restrict__ db, int Co, int Ci, long P, int B) {
-    const int co = blockIdx.y, ci = blockIdx.z;   // ci == Ci: bias
-    __shared__ float red[256];
-    float acc = 0.f;
-    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long)B * P; idx += (long)gridDim.x * blockDim.x) {
-        const int b = (int)(idx / P);
-        const long p = idx % P;
-        const float g = dY[((long)b * Co + co) * P + p];
-        acc += ci < Ci ? g * ld(X, ((long)b * Ci + ci) * P + p) : g;
-    }
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int h = 128; h > 0; h >>= 1) {
-        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+__global__ void __launch_bounds__(256) k_wgrad(const float* __restrict__ dY, const SX* __restrict__ X,
+                                               float* __restrict__ dW, float* __restrict__ db, int Co, int Ci, long P,
+                                               int B) {
+    __shared__ float ys[32][kWgChunk + 1];
+    __shared__ float xs[32][kWgChunk + 1];
+    constexpr int J = (32 * 33 + 255) / 256;
+    const int nout = Co * (Ci + 1);
+    float acc[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) acc[j] = 0.f;
+    const long cps = (P + kWgChunk - 1) / kWgChunk;       // chunks per sample
+    for (long c = blockIdx.x; c < (long)B * cps; c += gridDim.x) {
+        const int b = (int)(c / cps);
+        const long p0 = (c % cps) * kWgChunk;
+        for (int e = threadIdx.x; e < Co * kWgChunk; e += blockDim.x) {
+            const int co = e / kWgChunk, pp = e % kWgChunk;
+            ys[co][pp] = p0 + pp < P ? dY[((long)b * Co + co) * P + p0 + pp] : 0.f;
+        }
+        for (int e = threadIdx.x; e < Ci * kWgChunk; e += blockDim.x) {
+            const int ci = e / kWgChunk, pp = e % kWgChunk;
+            xs[ci][pp] = p0 + pp < P ? ld(X, ((long)b * Ci + ci) * P + p0 + pp) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int o = threadIdx.x + 256 * j;
+            if (o < nout) {
+                const int co = o / (Ci + 1), ci = o % (Ci + 1);
+                float a = 0.f;
+                if (ci < Ci) {
+                    for (int pp = 0; pp < kWgChunk; ++pp) a += ys[co][pp] * xs[ci][pp];
+                } else {
+                    for (int pp = 0; pp < kWgChunk; ++pp) a += ys[co][pp];
+                }
+                acc[j] += a;
+            }
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0) atomicAdd(ci < Ci ? &dW[co * Ci + ci] : &db[co], red[0]);
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int o = threadIdx.x + 256 * j;
+        if (o < nout) {
+            const int co = o / (Ci + 1), ci = o % (Ci + 1);
+            atomicAdd(ci < Ci ? &dW[co * Ci + ci] : &db[co], acc[j]);
+        }
+    }
+}
+
+inline unsigned wgrad_grid(long P, int B) {
+    const long n = (long)B * ((P + kWgChunk - 1) / kWgChunk);
+    return (unsigned)(n < 1216 ? n : 1216);
 }
 
 // per-sample sums of (h - t)^2 and t^2
@@ -302,6 +463,17 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
     p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
+// inverse-x basis rows for k_layer_out: [2 kx] = c_kx cos / P, [2 kx + 1] = c_kx (-sin) / P
+__global__ void k_init_basis(const float2* twx, float* basis, int NX, int NY, int M) {
+    const double invP = 1.0 / ((double)NX * NY);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * M * NX; i += gridDim.x * blockDim.x) {
+        const int r = i / NX, x = i % NX, kx = r >> 1;
+        const float2 w = twx[(long)kx * NX + x];
+        const double c = (kx == 0 ? 1.0 : 2.0) * invP;
+        basis[i] = (float)(c * ((r & 1) ? w.y : w.x));
+    }
+}
+
 __global__ void k_init_tw(float2* twx, float2* twy, int NX, int NY, int M) {
     const int total = M * NX + 2 * M * NY;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
@@ -346,13 +518,15 @@ template <typename SS> int forward_t(mm_fno* f, const float* m, float* h, int B)
     for (int l = 0; l < f->L; ++l) {
         SS* vl = v + l * vs;
         float2* S = f->S + (long)l * f->max_batch * W * K;
-        k_dft_x<SS><<<g1((long)B * W * NY * M), kFT, 0, f->stream>>>(vl, f->A, f->twx, (long)B * W * NY, NX, M, 1.f, 1.f);
-        k_dft_y<<<g1((long)B * W * 2 * M * M), kFT, 0, f->stream>>>(f->A, S, f->twy, B * W, NY, M, 1, -1.f);
+        k_dft_x<SS><<<(unsigned)(((long)B * W * NY + kDxRows - 1) / kDxRows), 256, 0, f->stream>>>(
+            vl, f->A, f->twx, (long)B * W * NY, NX, M, 1.f, 1.f);
+        k_dft_y_modes<<<g1(8L * B * W * 2 * M * M), kFT, 0, f->stream>>>(f->A, S, f->twy, B * W, NY, M, -1.f);
         k_mix<<<g1((long)B * W * K), kFT, 0, f->stream>>>(S, (const float2*)(f->params + f->o_R[l]), f->T, B, W, K, 0);
         k_dft_y<<<g1((long)B * W * NY * M), kFT, 0, f->stream>>>(f->T, f->U, f->twy, B * W, NY, M, 0, 1.f);
-        k_layer_out<SS><<<g1((long)B * P), kFT, 0, f->stream>>>(vl, f->U, f->params + f->o_W[l], f->params + f->o_b[l],
-                                                                f->twx, a + l * vs, v + (l + 1) * vs, B, W, NY, NX, M,
-                                                                l == f->L - 1);
+        k_layer_out<SS><<<dim3((unsigned)NY, (unsigned)B, (unsigned)((NX + kLoTile - 1) / kLoTile)), 256,
+                          layer_out_smem(W, M), f->stream>>>(vl, f->U, f->params + f->o_W[l], f->params + f->o_b[l],
+                                                             f->basis, a + l * vs, v + (l + 1) * vs, B, W, NY, NX, M,
+                                                             l == f->L - 1);
         FNO_CHECK(f);
     }
     k_chan<SS, float><<<g1((long)B * P), kFT, 0, f->stream>>>(v + f->L * vs, f->params + f->o_Q, f->params + f->o_q, h, W,
@@ -371,8 +545,7 @@ template <typename SS> int backward_t(mm_fno* f, const float* dh, int B) {
     float* dv2 = dv + vs;
     float* G = f->grads;
     // projection: dQ += dh v_L^T, dq += sum dh, dv_L = Q^T dh
-    dim3 gq(64, 3, W + 1);
-    k_wgrad<SS><<<gq, 256, 0, f->stream>>>(dh, v + f->L * vs, G + f->o_Q, G + f->o_q, 3, W, P, B);
+    k_wgrad<SS><<<wgrad_grid(P, B), 256, 0, f->stream>>>(dh, v + f->L * vs, G + f->o_Q, G + f->o_q, 3, W, P, B);
     k_chan<float, float><<<g1((long)B * P), kFT, 0, f->stream>>>(dh, f->params + f->o_Q, nullptr, dv, 3, W, P, B, 1.f, 1);
     FNO_CHECK(f);
     for (int l = f->L - 1; l >= 0; --l) {
@@ -381,14 +554,13 @@ template <typename SS> int backward_t(mm_fno* f, const float* dh, int B) {
         // da = dv * GELU'(a)
         k_gelu_bwd<SS><<<g1((long)B * W * P), kFT, 0, f->stream>>>(dv, a + l * vs, (long)B * W * P, l == f->L - 1);
         // channel part
-        dim3 gw(64, W, W + 1);
-        k_wgrad<SS><<<gw, 256, 0, f->stream>>>(dv, vl, G + f->o_W[l], G + f->o_b[l], W, W, P, B);
+        k_wgrad<SS><<<wgrad_grid(P, B), 256, 0, f->stream>>>(dv, vl, G + f->o_W[l], G + f->o_b[l], W, W, P, B);
         k_chan<float, float><<<g1((long)B * P), kFT, 0, f->stream>>>(dv, f->params + f->o_W[l], nullptr, dv2, W, W, P, B,
                                                                      1.f, 1);
         // spectral part: dU = c / P sum_x da e^{-i theta}
-        k_dft_x<float><<<g1((long)B * W * NY * M), kFT, 0, f->stream>>>(dv, f->U, f->twx, (long)B * W * NY, NX, M,
-                                                                       1.f / (float)P, 2.f / (float)P);
-        k_dft_y<<<g1((long)B * W * 2 * M * M), kFT, 0, f->stream>>>(f->U, f->T, f->twy, B * W, NY, M, 1, -1.f);
+        k_dft_x<float><<<(unsigned)(((long)B * W * NY + kDxRows - 1) / kDxRows), 256, 0, f->stream>>>(
+            dv, f->U, f->twx, (long)B * W * NY, NX, M, 1.f / (float)P, 2.f / (float)P);
+        k_dft_y_modes<<<g1(8L * B * W * 2 * M * M), kFT, 0, f->stream>>>(f->U, f->T, f->twy, B * W, NY, M, -1.f);
         k_mix_grad<<<g1((long)W * W * K), kFT, 0, f->stream>>>(f->T, S, (float2*)(G + f->o_R[l]), B, W, K);
         // dS = R^H dT into U (free again; the stored spectra S stay intact for a later backward)
         k_mix<<<g1((long)B * W * K), kFT, 0, f->stream>>>(f->T, (const float2*)(f->params + f->o_R[l]), f->U, B, W, K, 1);
@@ -423,9 +595,10 @@ int mm_fno_create(mm_fno** out, int nx, int ny, int width, int modes, int layers
                   unsigned long long seed, void* stream) {
     if (!out) return fail(nullptr, MM_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
-    if (nx < 2 || ny < 2 || width < 1 || width > 32 || modes < 1 || 2 * modes > ny || modes > nx / 2 || layers < 1 ||
+    if (nx < 2 || ny < 2 || width < 1 || width > 32 || modes < 1 || modes > kMaxModes || 2 * modes > ny ||
+        modes > nx / 2 || layers < 1 ||
         max_batch < 1)
-        return fail(nullptr, MM_ERR_INVALID_ARG, "FNO sizes: width <= 32, 2 modes <= ny, modes <= nx / 2");
+        return fail(nullptr, MM_ERR_INVALID_ARG, "FNO sizes: width <= 32, modes <= 32, 2 modes <= ny, modes <= nx / 2");
     mm_fno* f = new mm_fno();
     f->nx = nx;
     f->ny = ny;
@@ -474,6 +647,7 @@ int mm_fno_create(mm_fno** out, int nx, int ny, int width, int modes, int layers
     A(&f->dv, 2 * (size_t)vs * 4);
     A((void**)&f->twx, (size_t)modes * nx * sizeof(float2));
     A((void**)&f->twy, (size_t)2 * modes * ny * sizeof(float2));
+    A((void**)&f->basis, (size_t)2 * modes * nx * sizeof(float));
     A((void**)&f->red, (size_t)2 * max_batch * sizeof(double));
     if (!ok) {
         cudaGetLastError();
@@ -499,7 +673,15 @@ int mm_fno_create(mm_fno** out, int nx, int ny, int width, int modes, int layers
     if (ce == cudaSuccess) ce = cudaMemset(f->adam_m, 0, o * 4);
     if (ce == cudaSuccess) ce = cudaMemset(f->adam_v, 0, o * 4);
     k_init_tw<<<64, 256, 0, f->stream>>>(f->twx, f->twy, nx, ny, modes);
+    k_init_basis<<<64, 256, 0, f->stream>>>(f->twx, f->basis, nx, ny, modes);
     if (ce == cudaSuccess) ce = cudaGetLastError();
+    // the layer-output GEMM keeps its K x 256 operand in dynamic shared memory
+    if (ce == cudaSuccess)
+        ce = cudaFuncSetAttribute(k_layer_out<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)layer_out_smem(32, kMaxModes));
+    if (ce == cudaSuccess)
+        ce = cudaFuncSetAttribute(k_layer_out<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)layer_out_smem(32, kMaxModes));
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(f->stream);
     if (ce != cudaSuccess) {
         mm_fno_destroy(f);
@@ -513,7 +695,8 @@ void mm_fno_destroy(mm_fno* f) {
     if (!f) return;
     cudaSetDevice(f->device);
     cudaStreamSynchronize(f->stream);
-    void* ptrs[] = {f->params, f->grads, f->adam_m, f->adam_v, f->v, f->a, f->S, f->A, f->T, f->U, f->dv, f->twx, f->twy, f->red};
+    void* ptrs[] = {f->params, f->grads, f->adam_m, f->adam_v, f->v,   f->a,     f->S,  f->A,
+                    f->T,      f->U,     f->dv,     f->twx,    f->twy, f->basis, f->red};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete f;
@@ -537,8 +720,8 @@ int mm_fno_backward(mm_fno* f, const void* m, const void* dh, int batch) {
     // lift: dP += dv_0 m^T, dp += sum dv_0 (dv_0 ends in the buffer the last swap selected)
     const long vs = (long)f->max_batch * f->W * f->P;
     float* dv0 = (float*)f->dv + ((f->L % 2) ? vs : 0);
-    dim3 gp(64, f->W, 4);
-    k_wgrad<float><<<gp, 256, 0, f->stream>>>(dv0, (const float*)m, f->grads + f->o_P, f->grads + f->o_p, f->W, 3, f->P, batch);
+    k_wgrad<float><<<wgrad_grid(f->P, batch), 256, 0, f->stream>>>(dv0, (const float*)m, f->grads + f->o_P,
+                                                                    f->grads + f->o_p, f->W, 3, f->P, batch);
     FNO_CHECK(f);
     return MM_OK;
 }
