@@ -70,6 +70,20 @@ def dist_env():
     return world, rank, local
 
 
+def reduce_over_ranks(dist, ms, evals, accepted, device):
+    """Replicas: the slowest rank's timed region and the work of all ranks,
+    (max ms, sum of field evaluations, sum of accepted steps)."""
+    if dist is None:
+        return ms, float(evals), float(accepted)
+    import torch
+    t = torch.tensor([ms, float(evals), float(accepted)], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1]), float(sm[2])
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -407,15 +421,7 @@ def run_ours(args):
     ktimes = {name: mm.mm_kernel_time(ctx, k) for k, name in enumerate(mm.KERNEL_NAMES)}
     mm.mm_enable_kernel_timing(ctx, False)
     evals = ktimes["zconv"][1]           # one z-pass launch per demag evaluation
-    tot = torch.tensor([ms, float(evals), float(accepted)], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        mx = tot.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm_ = tot.clone()
-        dist.all_reduce(sm_, op=dist.ReduceOp.SUM)
-        ms_max, evals_all, acc_all = float(mx[0]), float(sm_[1]), float(sm_[2])
-    else:
-        ms_max, evals_all, acc_all = ms, float(evals), float(accepted)
+    ms_max, evals_all, acc_all = reduce_over_ranks(dist, ms, evals, accepted, "cuda")
     value = evals_all / (ms_max / 1e3)
     mcell = acc_all * N / (ms_max / 1e3) / 1e6
 
