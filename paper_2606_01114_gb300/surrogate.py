@@ -143,6 +143,30 @@ def gain(ctx, f, film, seeds, t_max, torque_tol, k_exact, bound, torque_exact):
     return rows
 
 
+def timing(film, width, modes, layers, batch, bf16=True):
+    """Kernel timing of the network alone: a batch-1 evaluation and one
+    training step (forward, loss, backward, Adam) at `batch`, random data."""
+    nx, ny = film["n"][0], film["n"][1]
+    f = mm_fno_create(nx, ny, width=width, modes=modes, layers=layers, store_bf16=bf16, max_batch=batch, seed=1)
+    m = torch.randn(1, 3, ny, nx, device="cuda")
+    h = torch.empty_like(m)
+    fwd_ms = per_eval_ms(lambda: mm_fno_forward(f, m, h), reps=100)
+    mb = torch.randn(batch, 3, ny, nx, device="cuda")
+    hb, dh = torch.empty_like(mb), torch.empty_like(mb)
+    state = {"s": 0}
+
+    def step():
+        state["s"] += 1
+        mm_fno_forward(f, mb, hb)
+        mm_fno_loss(f, hb, mb, dh)
+        mm_fno_zero_grad(f)
+        mm_fno_backward(f, mb, dh)
+        mm_fno_adam_step(f, 1e-3, step=state["s"])
+    step_ms = per_eval_ms(step, reps=20)
+    mm_fno_destroy(f)
+    return {"forward_batch1_ms": fwd_ms, f"train_step_batch{batch}_ms": step_ms}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--trajectories", type=int, default=400)
@@ -161,8 +185,13 @@ def main(argv=None):
     ap.add_argument("--bound", type=float, default=1e-3)
     ap.add_argument("--torque-exact", type=float, default=1e-2)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--timing", action="store_true", help="time the network's kernels only and exit")
     a = ap.parse_args(argv)
     film = FILM
+    if a.timing:
+        res = timing(film, a.width, a.modes, a.layers, a.batch, bf16=not a.fp32_storage)
+        print(json.dumps(res), flush=True)
+        return res
     ctx = film_context(film)
     res = {"film": {k: list(v) if isinstance(v, tuple) else v for k, v in film.items()}, "args": vars(a)}
 
