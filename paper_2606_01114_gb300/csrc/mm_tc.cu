@@ -15,6 +15,7 @@
 // raises the library's device status and frees its tensor memory.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 
@@ -32,6 +33,10 @@ constexpr long kTcWaitLimit = 1L << 22;
 // ([N][K] values, hi and lo parts), built once per device
 __device__ float g_dft_f32[2][2][kTcN * kTcK];            // [dir][hi/lo]
 __device__ __nv_bfloat16 g_dft_bf16[2][2][kTcN * kTcK];
+// the same matrices as shared-memory images (K-major canonical layout, hi
+// then lo), copied into a block with 16-byte loads
+__device__ __align__(16) unsigned char g_bimg_tf32[2][2 * kTcN * kTcK * 4];
+__device__ __align__(16) unsigned char g_bimg_bf16[2][2 * kTcN * kTcK * 2];
 __device__ int g_tc_status;
 
 bool g_tables_ready[64] = {false};
@@ -60,6 +65,20 @@ __global__ void k_init_dft_tables() {
         const __nv_bfloat16 hb = __float2bfloat16_rn((float)v);
         g_dft_bf16[d][0][e] = hb;
         g_dft_bf16[d][1][e] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(hb)));
+    }
+}
+
+template <int ES> __device__ __forceinline__ int kmajor_off(int r, int k, int K);
+
+__global__ void k_init_dft_images() {
+    for (int idx = threadIdx.x + blockIdx.x * blockDim.x; idx < 2 * kTcN * kTcK; idx += blockDim.x * gridDim.x) {
+        const int d = idx / (kTcN * kTcK), e = idx % (kTcN * kTcK);
+        const int j = e / kTcK, kk = e % kTcK;
+        const int o4 = kmajor_off<4>(j, kk, kTcK), o2 = kmajor_off<2>(j, kk, kTcK);
+        *reinterpret_cast<float*>(&g_bimg_tf32[d][o4]) = g_dft_f32[d][0][e];
+        *reinterpret_cast<float*>(&g_bimg_tf32[d][kTcN * kTcK * 4 + o4]) = g_dft_f32[d][1][e];
+        *reinterpret_cast<__nv_bfloat16*>(&g_bimg_bf16[d][o2]) = g_dft_bf16[d][0][e];
+        *reinterpret_cast<__nv_bfloat16*>(&g_bimg_bf16[d][kTcN * kTcK * 2 + o2]) = g_dft_bf16[d][1][e];
     }
 }
 
@@ -235,18 +254,23 @@ __global__ void __launch_bounds__(kTcLines) k_dft32_tc(const float2* __restrict_
 }
 
 // Four-step column transform of length L = 32 L2 for B = 128 / L2 adjacent
-// columns: level 1 (rows (t2, b), 32-point DFT over n1 of x[t2 + L2 n1]) is
-// one tensor-core GEMM of the 128 rows; on read-back each row is twiddled
-// by w_L^(t2 k1) and transposed through shared memory; level 2 (thread
-// (k1, b), L2-point DFT over n2 in registers) writes X[k1 + 32 k2].
-// PIN: the upper half of the input rows is zero (K = 32 real inputs);
-// POUT: only the lower half of the output rows is written.
+// columns, persistent over tiles (B columns of one plane each): level 1
+// (rows (t2, b), 32-point DFT over n1 of x[t2 + L2 n1]) is one tensor-core
+// GEMM of the 128 rows; on read-back each row is twiddled by w_L^(t2 k1) and
+// transposed through shared memory; level 2 (thread (k1, b), L2-point DFT
+// over n2 in registers) writes X[k1 + 32 k2].  The DFT-matrix operand and
+// the tensor memory are set up once per block; the line operands are split
+// into hi + lo and stored 16 bytes at a time.  PIN: the upper half of the
+// input rows is zero (K = 32 real inputs); POUT: only the lower half of the
+// output rows is written.
 template <int L2, int DIR, bool PIN, bool POUT, bool TF32>
 __global__ void __launch_bounds__(32 * (128 / L2))
-    k_cols_tc(const float2* in, float2* out, int Hx, ColGeom cg, const float2* __restrict__ tw) {
+    k_cols_tc(const float2* in, float2* out, int Hx, ColGeom cg, const float2* __restrict__ tw, int ntx,
+              long ntiles) {
     constexpr int B = 128 / L2, L = 32 * L2;
     constexpr int ES = TF32 ? 4 : 2;
     constexpr int KA = PIN ? 32 : 64;
+    constexpr int EPV = 16 / ES;                            // elements per 16-byte store
     using S = TcSmem<ES>;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* a_hi = smem;
@@ -261,11 +285,6 @@ __global__ void __launch_bounds__(32 * (128 / L2))
     const int m = B < 16 ? 16 / B - 1 : 0;
     const uint32_t mbar_a = (uint32_t)__cvta_generic_to_shared(mbar);
     const int dir_index = DIR < 0 ? 0 : 1;
-    const int col0 = blockIdx.x * B;
-    const int p = blockIdx.y;
-    const int pi = p % cg.n_inner, po = p / cg.n_inner;
-    const float2* ib = in + pi * cg.in_inner + po * cg.in_outer;
-    float2* ob = out + pi * cg.out_inner + po * cg.out_outer;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -274,115 +293,151 @@ __global__ void __launch_bounds__(32 * (128 / L2))
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_a));
-    for (int e = tid; e < kTcN * kTcK; e += blockDim.x) {
-        const int j = e / kTcK, kk = e % kTcK;
-        if (kk >= KA) continue;
-        const int o = kmajor_off<ES>(j, kk, kTcK);
-        if constexpr (TF32) {
-            *reinterpret_cast<float*>(b_hi + o) = g_dft_f32[dir_index][0][e];
-            *reinterpret_cast<float*>(b_lo + o) = g_dft_f32[dir_index][1][e];
-        } else {
-            *reinterpret_cast<__nv_bfloat16*>(b_hi + o) = g_dft_bf16[dir_index][0][e];
-            *reinterpret_cast<__nv_bfloat16*>(b_lo + o) = g_dft_bf16[dir_index][1][e];
-        }
-    }
-    const int t2 = tid / B, bb = tid % B;
-    const bool act = col0 + bb < Hx;
-    if (tid < kTcLines) {
-        float2 v[KA / 2];
-#pragma unroll
-        for (int n1 = 0; n1 < KA / 2; ++n1)
-            v[n1] = act ? ib[(long)(t2 + L2 * n1) * cg.rs_in + col0 + bb] : make_float2(0.f, 0.f);
-#pragma unroll
-        for (int n1 = 0; n1 < KA / 2; ++n1) {
-            const float xs[2] = {v[n1].x, v[n1].y};
-#pragma unroll
-            for (int part = 0; part < 2; ++part) {
-                const int o = kmajor_off<ES>(tid, 2 * n1 + part, kTcK);
-                if constexpr (TF32) {
-                    const float h = tf32_round(xs[part]);
-                    *reinterpret_cast<float*>(a_hi + o) = h;
-                    *reinterpret_cast<float*>(a_lo + o) = tf32_round(xs[part] - h);
-                } else {
-                    const __nv_bfloat16 h = __float2bfloat16_rn(xs[part]);
-                    *reinterpret_cast<__nv_bfloat16*>(a_hi + o) = h;
-                    *reinterpret_cast<__nv_bfloat16*>(a_lo + o) = __float2bfloat16_rn(xs[part] - __bfloat162float(h));
-                }
-            }
-        }
+    {
+        // B (hi then lo): one image copy
+        const uint4* src = reinterpret_cast<const uint4*>(TF32 ? g_bimg_tf32[dir_index] : g_bimg_bf16[dir_index]);
+        uint4* dst = reinterpret_cast<uint4*>(b_hi);
+        for (int e = tid; e < 2 * S::B_BYTES / 16; e += blockDim.x) dst[e] = src[e];
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    if (tid == 0) {
-        const uint32_t idesc = instr_desc<TF32>();
-        const uint32_t sbo = (kTcK / (16 / ES)) * 128;
-        const uint32_t A[2] = {(uint32_t)__cvta_generic_to_shared(a_hi), (uint32_t)__cvta_generic_to_shared(a_lo)};
-        const uint32_t Bm[2] = {(uint32_t)__cvta_generic_to_shared(b_hi), (uint32_t)__cvta_generic_to_shared(b_lo)};
-        const int pa[3] = {0, 0, 1}, pb[3] = {0, 1, 0};
-        constexpr int KMMA = TF32 ? 8 : 16;
-        uint32_t acc = 0;
-        for (int q = 0; q < 3; ++q)
-            for (int kc = 0; kc < KA / KMMA; ++kc) {
-                mma<TF32>(tmem, smem_desc(A[pa[q]] + kc * 256, 128, sbo), smem_desc(Bm[pb[q]] + kc * 256, 128, sbo), idesc,
-                          acc);
-                acc = 1;
-            }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_a)
-                     : "memory");
-    }
-    const bool ok = mbar_wait(mbar_a, 0);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!ok && (tid & 31) == 0) atomicCAS(&g_tc_status, 0, (int)MM_ERR_TIMEOUT);
-    if (ok && tid < kTcLines) {
-        uint32_t r[64];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
-            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
-            "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
-            "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
-              "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
-              "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
-              "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
-              "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        // all MMA reads of A are complete (mbarrier), so T may overwrite A
+    const int t2 = tid / B, bb = tid % B;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (long it = blockIdx.x; it < ntiles; it += gridDim.x, phase ^= 1u) {
+        const int col0 = (int)(it % ntx) * B;
+        const int p = (int)(it / ntx);
+        const int pi = p % cg.n_inner, po = p / cg.n_inner;
+        const float2* ib = in + pi * cg.in_inner + po * cg.in_outer;
+        float2* ob = out + pi * cg.out_inner + po * cg.out_outer;
+        const bool act = col0 + bb < Hx;
+        if (tid < kTcLines) {
+            float2 v[KA / 2];
 #pragma unroll
-        for (int k1 = 0; k1 < 32; ++k1) {
-            float2 y = make_float2(__uint_as_float(r[2 * k1]), __uint_as_float(r[2 * k1 + 1]));
-            if (k1 > 0) {
-                float2 w = tw[t2 * k1];
-                if (DIR > 0) w.y = -w.y;
-                y = cmul(y, w);
+            for (int n1 = 0; n1 < KA / 2; ++n1)
+                v[n1] = act ? ib[(long)(t2 + L2 * n1) * cg.rs_in + col0 + bb] : make_float2(0.f, 0.f);
+            // operand row tid: element kk = 2 n1 + part; EPV consecutive elements per 16-byte store
+#pragma unroll
+            for (int c = 0; c < KA / EPV; ++c) {
+                float xs[EPV];
+#pragma unroll
+                for (int q = 0; q < EPV; ++q) {
+                    const float2 z = v[(c * EPV + q) >> 1];
+                    xs[q] = (q & 1) ? z.y : z.x;
+                }
+                const int o = kmajor_off<ES>(tid, c * EPV, kTcK);
+                if constexpr (TF32) {
+                    float h[4], l[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        h[q] = tf32_round(xs[q]);
+                        l[q] = tf32_round(xs[q] - h[q]);
+                    }
+                    *reinterpret_cast<float4*>(a_hi + o) = make_float4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<float4*>(a_lo + o) = make_float4(l[0], l[1], l[2], l[3]);
+                } else {
+                    uint32_t hw[4], lw[4];   // element q at byte 2 q of the 16-byte slot
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const __nv_bfloat16 h0 = __float2bfloat16_rn(xs[2 * q]);
+                        const __nv_bfloat16 h1 = __float2bfloat16_rn(xs[2 * q + 1]);
+                        const __nv_bfloat162 hp = __halves2bfloat162(h0, h1);
+                        const __nv_bfloat162 lp = __halves2bfloat162(
+                            __float2bfloat16_rn(xs[2 * q] - __bfloat162float(h0)),
+                            __float2bfloat16_rn(xs[2 * q + 1] - __bfloat162float(h1)));
+                        hw[q] = *reinterpret_cast<const uint32_t*>(&hp);
+                        lw[q] = *reinterpret_cast<const uint32_t*>(&lp);
+                    }
+                    *reinterpret_cast<uint4*>(a_hi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    *reinterpret_cast<uint4*>(a_lo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                }
             }
-            T[((k1 * L2) + (t2 ^ (k1 & m))) * B + bb] = y;
         }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            const uint32_t idesc = instr_desc<TF32>();
+            const uint32_t sbo = (kTcK / (16 / ES)) * 128;
+            const uint32_t A[2] = {(uint32_t)__cvta_generic_to_shared(a_hi), (uint32_t)__cvta_generic_to_shared(a_lo)};
+            const uint32_t Bm[2] = {(uint32_t)__cvta_generic_to_shared(b_hi), (uint32_t)__cvta_generic_to_shared(b_lo)};
+            const int pa[3] = {0, 0, 1}, pb[3] = {0, 1, 0};
+            constexpr int KMMA = TF32 ? 8 : 16;
+            uint32_t acc = 0;
+            for (int q = 0; q < 3; ++q)
+                for (int kc = 0; kc < KA / KMMA; ++kc) {
+                    mma<TF32>(tmem, smem_desc(A[pa[q]] + kc * 256, 128, sbo), smem_desc(Bm[pb[q]] + kc * 256, 128, sbo),
+                              idesc, acc);
+                    acc = 1;
+                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_a)
+                         : "memory");
+        }
+        ok = mbar_wait(mbar_a, phase);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (__syncthreads_or(!ok)) {
+            ok = false;
+            break;
+        }
+        if (tid < kTcLines) {
+            uint32_t r[64];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+                "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+                "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                  "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                  "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+                  "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+                  "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+                  "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+                  "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            // all MMA reads of A are complete (mbarrier), so T may overwrite A
+#pragma unroll
+            for (int k1 = 0; k1 < 32; ++k1) {
+                float2 y = make_float2(__uint_as_float(r[2 * k1]), __uint_as_float(r[2 * k1 + 1]));
+                if (k1 > 0) {
+                    float2 w = tw[t2 * k1];
+                    if (DIR > 0) w.y = -w.y;
+                    y = cmul(y, w);
+                }
+                T[((k1 * L2) + (t2 ^ (k1 & m))) * B + bb] = y;
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        {
+            const int k1 = tid / B, b2 = tid % B;
+            const bool act2 = col0 + b2 < Hx;
+            float2 u[L2];
+#pragma unroll
+            for (int n2 = 0; n2 < L2; ++n2) u[n2] = T[((k1 * L2) + (n2 ^ (k1 & m))) * B + b2];
+            dif<L2, DIR, false>(u);
+            constexpr int NOUT = POUT ? L2 / 2 : L2;
+            if (act2) {
+#pragma unroll
+                for (int k2 = 0; k2 < NOUT; ++k2) ob[(long)(k1 + 32 * k2) * cg.rs_out + col0 + b2] = u[dif_pos<L2>(k2)];
+            }
+        }
+        __syncthreads();   // T (the A space) is free for the next tile
+    }
+    if (!ok) {
+        if ((tid & 31) == 0) atomicCAS(&g_tc_status, 0, (int)MM_ERR_TIMEOUT);
+        mbar_wait(mbar_a, phase);   // let an MMA still in flight finish before the memory goes (bounded)
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcN));
-    {
-        const int k1 = tid / B, b2 = tid % B;
-        const bool act2 = col0 + b2 < Hx;
-        float2 u[L2];
-#pragma unroll
-        for (int n2 = 0; n2 < L2; ++n2) u[n2] = T[((k1 * L2) + (n2 ^ (k1 & m))) * B + b2];
-        dif<L2, DIR, false>(u);
-        constexpr int NOUT = POUT ? L2 / 2 : L2;
-        if (act2 && ok) {
-#pragma unroll
-            for (int k2 = 0; k2 < NOUT; ++k2) ob[(long)(k1 + 32 * k2) * cg.rs_out + col0 + b2] = u[dif_pos<L2>(k2)];
-        }
-    }
 }
 
 template <int L2, int DIR, bool TF32>
@@ -392,8 +447,17 @@ int launch_cols_tc(mm_ctx* ctx, const float2* in, float2* out, int nplanes, ColG
     auto fn = k_cols_tc<L2, DIR, (DIR < 0), (DIR > 0), TF32>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return fail(ctx, MM_ERR_CUDA, "tensor-core pass setup: %s", cudaGetErrorString(e));
-    dim3 grid((unsigned)((ctx->Hx + B - 1) / B), (unsigned)nplanes);
-    fn<<<grid, 32 * B, bytes, ctx->stream>>>(in, out, ctx->Hx, g, tw);
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * B, bytes);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e != cudaSuccess || per_sm < 1) return fail(ctx, MM_ERR_CUDA, "tensor-core pass: no resident block");
+    const int ntx = (ctx->Hx + B - 1) / B;
+    const long ntiles = (long)ntx * nplanes;
+    // tiles per block (measured): two for the 128-thread L = 1024 pass (one:
+    // more operand staging per line; more: less overlap); the 256-thread
+    // L = 512 pass runs persistent, one block per resident slot
+    const long grid = L2 == 32 ? (ntiles + 1) / 2 : std::min<long>(ntiles, (long)per_sm * sms);
+    fn<<<(unsigned)grid, 32 * B, bytes, ctx->stream>>>(in, out, ctx->Hx, g, tw, ntx, ntiles);
     MM_LAUNCH_CHECK(ctx);
     return MM_OK;
 }
@@ -403,6 +467,7 @@ int ensure_tables(int dev, cudaStream_t st) {
     std::lock_guard<std::mutex> lock(g_tables_mutex);
     if (!g_tables_ready[dev]) {
         k_init_dft_tables<<<16, 256, 0, st>>>();
+        k_init_dft_images<<<16, 256, 0, st>>>();
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return fail(nullptr, MM_ERR_CUDA, "DFT table setup: %s", cudaGetErrorString(e));
