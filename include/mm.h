@@ -279,6 +279,16 @@ int mm_set_fft_mode(mm_ctx* ctx, int mode);
  * since the last check (waits for the stream). */
 int mm_tc_status(mm_ctx* ctx);
 
+/* Self-test of the library's bounded device waits (no paper counterpart):
+ * one block polls an mbarrier that nothing completes, `limit` times
+ * (1 .. 2^20), the same way the tensor-core kernels wait for their MMAs,
+ * gives up, and raises TIMEOUT in the device status.  The call reads the
+ * status, clears it again and returns MM_ERR_TIMEOUT when the wait gave up
+ * as designed (MM_OK would mean it did not); no GPU fault is involved and
+ * the library stays usable.  Uses one cudaMalloc of 4 bytes.  stream:
+ * cudaStream_t or NULL.  Errors: INVALID_ARG, CUDA. */
+int mm_tc_wait_selftest(long limit, void* stream);
+
 /* ---- Fourier-neural-operator surrogate of the demag field ------------------
  * Not in the paper: a learned stand-in for Eq. 4 on 2-D films (nz = 1), used
  * inside relax() with the exact field recomputed every k steps.  Network:

@@ -100,6 +100,7 @@ def _load():
         "mm_fno_set_output_scale": (I, [P, D]),
         "mm_set_dmi": (I, [P, D, I]),
         "mm_set_stt": (I, [P, D, D, D, D, P, D]),
+        "mm_tc_wait_selftest": (I, [L, P]),
         "mm_minimize_bb": (I, [P, P, D, L, LP]),
         "mm_relax_surrogate": (I, [P, P, P, D, D, L, I, D, D, DP, LP, LP]),
     }
@@ -355,6 +356,12 @@ def mm_dft32_tc(inp, out, mode=MM_TC_TF32, direction=-1, stream=None):
                          int(mode), int(direction), _stream_ptr(stream))
     if rc != MM_OK:
         raise MMError(rc, lib.mm_last_error(None).decode())
+
+
+def mm_tc_wait_selftest(limit=1000, stream=None):
+    """Runs the bounded-wait self-test; returns its code (MM_ERR_TIMEOUT when
+    the wait gave up as designed) without raising."""
+    return int(_load().mm_tc_wait_selftest(int(limit), _stream_ptr(stream)))
 
 
 def mm_energy_noalloc(n, d, precision, Ms, A, Ku, u, h_ext, m, H_demag, stream=None):

@@ -116,8 +116,8 @@ __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uin
     }
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
-    for (long it = 0; it < kTcWaitLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, long limit = kTcWaitLimit) {
+    for (long it = 0; it < limit; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -128,6 +128,21 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
         if (ok) return true;
     }
     return false;
+}
+
+// Self-test of the bounded wait: the block initialises an mbarrier that
+// expects one arrival nobody makes and polls it `limit` times; the wait gives
+// up, raises TIMEOUT in the device status and the block returns.
+__global__ void k_wait_selftest(long limit, int* gave_up) {
+    __shared__ uint64_t bar;
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(&bar);
+    if (threadIdx.x == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a));
+    __syncthreads();
+    const bool ok = mbar_wait(a, 0, limit);
+    if (!ok && threadIdx.x == 0) {
+        atomicCAS(&g_tc_status, 0, (int)MM_ERR_TIMEOUT);
+        *gave_up = 1;
+    }
 }
 
 // Shared memory of one tile: A hi/lo [128 x 64], B hi/lo [64 x 64] (element
@@ -519,6 +534,33 @@ extern "C" int mm_tc_status(mm_ctx* ctx) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return fail(ctx, MM_ERR_CUDA, "%s", cudaGetErrorString(e));
     if (status) return fail(ctx, status, "a tensor-core wait timed out");
+    return MM_OK;
+}
+
+extern "C" int mm_tc_wait_selftest(long limit, void* stream) {
+    if (limit < 1 || limit > (1L << 20)) return fail(nullptr, MM_ERR_INVALID_ARG, "mm_tc_wait_selftest: limit in 1..2^20");
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    cudaError_t e = st ? cudaStreamGetDevice(st, &dev) : cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaSetDevice(dev);
+    int* flag = nullptr;
+    int gave_up = 0, status = 0;
+    const int zero = 0;
+    if (e == cudaSuccess) e = cudaMalloc(&flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(g_tc_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        k_wait_selftest<<<1, 32, 0, st>>>(limit, flag);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&gave_up, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbolAsync(&status, g_tc_status, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
+    // clear the status again: the self-test leaves the library usable
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(g_tc_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (flag) cudaFree(flag);
+    if (e != cudaSuccess) return fail(nullptr, MM_ERR_CUDA, "mm_tc_wait_selftest: %s", cudaGetErrorString(e));
+    if (gave_up && status == MM_ERR_TIMEOUT) return fail(nullptr, MM_ERR_TIMEOUT, "bounded wait gave up as intended");
     return MM_OK;
 }
 

@@ -346,3 +346,23 @@ def test_demag_film512_sampled_cells(prec):
     sel = np.stack([got[:, z, y, x] for (x, y, z) in targets], axis=1)
     assert rel_l2(sel, ref) < TOL[prec]
     mm.mm_destroy(ctx)
+
+
+def test_error_paths_underflow_and_step_cap():
+    """RKF45 with an unreachable tolerance shrinks dt below 1e-20 s and
+    reports DT_UNDERFLOW; relax() that hits max_steps first reports
+    NOT_CONVERGED; both leave the context usable."""
+    n, d = (8, 8, 2), (2.5e-9, 2.5e-9, 3e-9)
+    p = micromag.Problem(n, d, alpha=0.02)
+    ctx = gpu_ctx(p, mm.MM_F64)
+    md = dev(wl.random_unit(n, seed=31), mm.MM_F64)
+    with pytest.raises(mm.MMError) as e:
+        mm.mm_llg_step(ctx, md, 0.0, 1e-13, mm.MM_RKF45, tol=1e-300)
+    assert e.value.code == mm.MM_ERR_DT_UNDERFLOW
+    md = dev(wl.random_unit(n, seed=31), mm.MM_F64)
+    with pytest.raises(mm.MMError) as e:
+        mm.mm_relax(ctx, md, t_max=1e-6, torque_tol=1e-12, max_steps=20)
+    assert e.value.code == mm.MM_ERR_NOT_CONVERGED
+    t, dt, err = mm.mm_llg_step(ctx, md, 0.0, 1e-14, mm.MM_RKF45, tol=1e-5)   # still usable
+    assert t > 0 and err <= 1e-5
+    mm.mm_destroy(ctx)

@@ -123,3 +123,16 @@ def test_cube256_per_field_errors_and_speed():
     assert rows["bf16x3"][0]["demag"] < 1e-4
     del ref
     torch.cuda.empty_cache()
+
+
+def test_bounded_wait_gives_up_and_reports_timeout():
+    """A wait on an mbarrier that nothing completes gives up after its poll
+    limit, raises TIMEOUT in the device status (read back and cleared by the
+    call), and the tensor-core path keeps working afterwards."""
+    assert mm.mm_tc_wait_selftest(1000) == mm.MM_ERR_TIMEOUT
+    assert mm.mm_tc_wait_selftest(1) == mm.MM_ERR_TIMEOUT
+    x = torch.randn(64, 32, dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    mm.mm_dft32_tc(x, y, mm.MM_TC_TF32, -1)      # raises if a timeout were still pending
+    ref = torch.fft.fft(x.to(torch.complex128), dim=1)
+    assert float((y.to(torch.complex128) - ref).abs().max() / ref.abs().max()) < 1e-5
