@@ -161,6 +161,18 @@ def ingest_ncu(csv_path, precision, workload):
     out["_note"] = ("DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an ncu "
                     "capture; valid while the kernel family's sources hash to source_sha")
     for k, prefix in NCU_NAMES.items():
+        if k == "stage":
+            # the byte model is the average over the RKF45 stages: average the captured stage launches
+            got = [r for r in data if (lambda mt: mt and mt.group(1).startswith(prefix))(
+                re.search(r"(k_\w+)<([^>]*)>", r[col["Kernel Name"]]))]
+            if got:
+                rd = sum(to_bytes(r, "dram__bytes_read.sum") for r in got) / len(got)
+                wr = sum(to_bytes(r, "dram__bytes_write.sum") for r in got) / len(got)
+                name = re.search(r"(k_\w+)<", got[0][col["Kernel Name"]]).group(1)
+                out[f"{k}/{precision}"] = {"kernel": f"{name} (average of {len(got)} stage launches)",
+                                           "workload": workload, "bytes_per_launch": int(rd + wr), "read": int(rd),
+                                           "write": int(wr), "source_sha": source_hash(k)}
+            continue
         for r in data:
             mt = re.search(r"(k_\w+)<([^>]*)>", r[col["Kernel Name"]])
             if not mt or not mt.group(1).startswith(prefix):
