@@ -373,22 +373,80 @@ __global__ void k_cols_direct(const C_t<T>* __restrict__ in, C_t<T>* __restrict_
 // K4 for Pz <= 32: one thread per (component, column) holds its whole z line
 // in registers; forward DFT (upper half zero), the 3x3 product through shared
 // memory (each thread forms its own component from all three), inverse DFT,
-// keep the nz un-padded rows.  Block: 3 x B threads, B = 2^lgB columns.
+// keep the nz un-padded rows.  Block: 3 warps x 32 columns; warp c is tensor
+// row c.  The block's kernel octant rows (6 components x (Pz/2 + 1) kz rows
+// of 32 columns) are staged once in shared memory by 16-byte asynchronous
+// copies that land while the forward DFT runs, so the product reads each
+// value at a compile-time offset.  Parity signs: xy is odd in ky, xz odd in
+// kz, yz odd in both (the parity of the Newell components); the kz sign is
+// compile-time per row, the ky sign sy is applied once to the y spectrum and
+// to row y's result.
+constexpr int kZB = 32;   // columns per z-pass block
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// row C of the symmetric tensor against the staged spectra S [3][PZ][kZB]
+// (the y spectrum already multiplied by sy) and kernel rows K [6][PZ/2+1][kZB]
+// (storage order xx, yy, zz, xy, xz, yz); v[kz] <- -(N m)_C, row 1 divided by sy
+template <int PZ, int C>
+__device__ __forceinline__ void zconv_product(float2 (&v)[PZ], const float2* S, const float* K, int b) {
+    constexpr int PZ2 = PZ / 2 + 1;
+    constexpr int I0 = C == 0 ? 0 : C == 1 ? 3 : 4;
+    constexpr int I1 = C == 0 ? 3 : C == 1 ? 1 : 5;
+    constexpr int I2 = C == 0 ? 4 : C == 1 ? 5 : 2;
+#pragma unroll
+    for (int kz = 0; kz < PZ; ++kz) {
+        const int kzp = kz <= PZ / 2 ? kz : PZ - kz;
+        const bool odd = kz > PZ / 2;
+        float a0 = K[(I0 * PZ2 + kzp) * kZB + b];
+        float a1 = K[(I1 * PZ2 + kzp) * kZB + b];
+        float a2 = K[(I2 * PZ2 + kzp) * kZB + b];
+        if (odd) {
+            if (C == 2) {
+                a0 = -a0;
+                a1 = -a1;
+            } else {
+                a2 = -a2;
+            }
+        }
+        const float2 mx = S[kz * kZB + b], my = S[(PZ + kz) * kZB + b], mz = S[(2 * PZ + kz) * kZB + b];
+        v[kz] = make_float2(-(a0 * mx.x + a1 * my.x + a2 * mz.x), -(a0 * mx.y + a1 * my.y + a2 * mz.y));
+    }
+}
+
 template <int PZ>
-__global__ void __launch_bounds__(256)
-    k_zconv_reg(float2* buf, const float* __restrict__ kern, int Py, int Hs, int c0, int Hx, int Py2, int lgB) {
+__global__ void __launch_bounds__(3 * kZB)
+    k_zconv_reg(float2* buf, const float* __restrict__ kern, int Py, int Hs, int c0, int Hx, int Py2) {
     constexpr int NZ = PZ > 1 ? PZ / 2 : 1;
     constexpr int PZ2 = PZ / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* S = reinterpret_cast<float2*>(smem_raw);      // [3][PZ][B]
-    const int B = 1 << lgB;
-    const int c = threadIdx.x >> lgB, b = threadIdx.x & (B - 1);
-    const int col = c0 + (blockIdx.x << lgB) + b;   // columns c0 .. Hx-1
+    float2* S = reinterpret_cast<float2*>(smem_raw);                                // [3][PZ][kZB]
+    float* K = reinterpret_cast<float*>(smem_raw + 3 * PZ * kZB * sizeof(float2));  // [6][PZ2][kZB]
+    const int c = threadIdx.x / kZB, b = threadIdx.x % kZB;
+    const int col0 = c0 + blockIdx.x * kZB;   // columns c0 .. Hx-1, c0 % 4 == 0
+    const int col = col0 + b;
     // block rows in the order 0, Py/2, 1, Py-1, 2, Py-2, ...: the two rows that
     // share an octant row of the kernel run back to back, so its second read
     // comes from L2
     const int j = blockIdx.y;
     const int ky = j == 0 ? 0 : j == 1 ? (Py >> 1) : ((j & 1) ? Py - (j >> 1) : (j >> 1));
+    const int kyp = ky <= (Py >> 1) ? ky : Py - ky;
+    const bool yodd = ky > (Py >> 1);
+    {
+        // 16-byte chunks of the octant rows; a chunk that starts below Hx ends
+        // inside the row (Hs is a multiple of 16, chunk starts of 4)
+        const long kstride = (long)PZ2 * Py2 * Hs, kzs = (long)Py2 * Hs;
+        const float* kb = kern + (long)kyp * Hs + col0;
+        for (int q = threadIdx.x; q < 6 * PZ2 * (kZB / 4); q += 3 * kZB) {
+            const int chunk = q % (kZB / 4), row = q / (kZB / 4);
+            const int comp = row / PZ2, kzp = row - comp * PZ2;
+            if (col0 + 4 * chunk < Hx) cp_async16(K + row * kZB + 4 * chunk, kb + comp * kstride + kzp * kzs + 4 * chunk);
+        }
+    }
     const bool act = col < Hx;
     const long zstride = (long)Py * Hs;
     float2* p = buf + c * (NZ * zstride) + (long)ky * Hs + col;
@@ -396,36 +454,25 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int z = 0; z < NZ; ++z) v[z] = act ? p[z * zstride] : make_float2(0.f, 0.f);
     dif<PZ, -1, (PZ > 1)>(v);
+    if (c == 1 && yodd) {
 #pragma unroll
-    for (int kz = 0; kz < PZ; ++kz) S[(c * PZ + kz) * B + b] = v[dif_pos<PZ>(kz)];
-    __syncthreads();
-    const int kyp = ky <= (Py >> 1) ? ky : Py - ky;
-    const float sy = ky > (Py >> 1) ? -1.f : 1.f;
-    const long kstride = (long)PZ2 * Py2 * Hs;
-    // row c of the symmetric tensor: components (xx, xy, xz), (xy, yy, yz), (xz, yz, zz)
-    const int i0 = c == 0 ? 0 : c == 1 ? 3 : 4;
-    const int i1 = c == 0 ? 3 : c == 1 ? 1 : 5;
-    const int i2 = c == 0 ? 4 : c == 1 ? 5 : 2;
-    const float* kc = kern + ((long)kyp * Hs + (act ? col : 0));
-#pragma unroll
-    for (int kz = 0; kz < PZ; ++kz) {
-        const int kzp = kz <= PZ / 2 ? kz : PZ - kz;
-        const float sz = kz > PZ / 2 ? -1.f : 1.f;
-        // parity signs: xy odd in ky, xz odd in kz, yz odd in both
-        const float s0 = c == 0 ? 1.f : c == 1 ? sy : sz;
-        const float s1 = c == 0 ? sy : c == 1 ? 1.f : sy * sz;
-        const float s2 = c == 0 ? sz : c == 1 ? sy * sz : 1.f;
-        const long ko = (long)kzp * Py2 * Hs;
-        const float n0 = s0 * __ldg(kc + i0 * kstride + ko);
-        const float n1 = s1 * __ldg(kc + i1 * kstride + ko);
-        const float n2 = s2 * __ldg(kc + i2 * kstride + ko);
-        const float2 mx = S[kz * B + b], my = S[(PZ + kz) * B + b], mz = S[(2 * PZ + kz) * B + b];
-        v[kz] = make_float2(-(n0 * mx.x + n1 * my.x + n2 * mz.x), -(n0 * mx.y + n1 * my.y + n2 * mz.y));
+        for (int kz = 0; kz < PZ; ++kz) v[kz] = make_float2(-v[kz].x, -v[kz].y);
     }
+#pragma unroll
+    for (int kz = 0; kz < PZ; ++kz) S[(c * PZ + kz) * kZB + b] = v[dif_pos<PZ>(kz)];
+    cp_async_wait_all();
+    __syncthreads();
+    if (c == 0) zconv_product<PZ, 0>(v, S, K, b);
+    else if (c == 1) zconv_product<PZ, 1>(v, S, K, b);
+    else zconv_product<PZ, 2>(v, S, K, b);
     dif<PZ, +1, false>(v);
     if (act) {
+        const float sg = (c == 1 && yodd) ? -1.f : 1.f;
 #pragma unroll
-        for (int z = 0; z < NZ; ++z) p[z * zstride] = v[dif_pos<PZ>(z)];
+        for (int z = 0; z < NZ; ++z) {
+            const float2 o = v[dif_pos<PZ>(z)];
+            p[z * zstride] = make_float2(sg * o.x, sg * o.y);
+        }
     }
 }
 
@@ -836,12 +883,13 @@ int run_cols(mm_ctx* ctx, const C_t<T>* in, C_t<T>* out, int L, int nin, int nou
 
 template <int PZ>
 int launch_zconv_reg_t(mm_ctx* ctx, float2* buf, const float* kern, int c0, int c1) {
-    constexpr int lgB = 5;   // 32 columns, 3 x 32 threads
-    const size_t smem = (size_t)3 * PZ * (1 << lgB) * sizeof(float2);
+    constexpr int PZ2 = PZ / 2 + 1;
+    const size_t smem = (size_t)3 * PZ * kZB * sizeof(float2) + (size_t)6 * PZ2 * kZB * sizeof(float);
+    if (c0 % 4) return fail(ctx, MM_ERR_INVALID_ARG, "z pass: first column %d not a multiple of 4", c0);
     int rc = set_smem(ctx, (const void*)k_zconv_reg<PZ>, smem);
     if (rc) return rc;
-    dim3 grid((unsigned)((c1 - c0 + 31) / 32), (unsigned)ctx->Py);
-    k_zconv_reg<PZ><<<grid, 3 << lgB, smem, ctx->stream>>>(buf, kern, ctx->Py, ctx->Hs, c0, c1, ctx->Py2, lgB);
+    dim3 grid((unsigned)((c1 - c0 + kZB - 1) / kZB), (unsigned)ctx->Py);
+    k_zconv_reg<PZ><<<grid, 3 * kZB, smem, ctx->stream>>>(buf, kern, ctx->Py, ctx->Hs, c0, c1, ctx->Py2);
     MM_LAUNCH_CHECK(ctx);
     return MM_OK;
 }

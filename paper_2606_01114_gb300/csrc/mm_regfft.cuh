@@ -11,6 +11,8 @@
 // the Taylor series on [0, pi/4] in double, rounded to the element type.
 #pragma once
 
+#include <type_traits>
+
 #include "mm_internal.cuh"
 
 namespace mm {
@@ -63,19 +65,55 @@ template <typename C> __host__ __device__ __forceinline__ C mul_dir_i(C a, int d
     return dir > 0 ? cmk<C>(-a.y, a.x) : cmk<C>(a.y, -a.x);
 }
 
-// natural-order small DFTs
+// Complex add and subtract of float2 values as one paired FP32 instruction
+// (add.rn.f32x2 / sub.rn.f32x2, sm_100 and later: each lane is rounded like
+// the scalar operation, so results are unchanged and the FADD count halves).
+// Other element types, and the host pass, use the scalar forms.
+template <typename C> __host__ __device__ __forceinline__ C padd(C a, C b) {
+#if defined(__CUDA_ARCH__)
+    if constexpr (std::is_same<C, float2>::value) {
+        float2 r;
+        asm("{\n\t.reg .b64 pa, pb, pr;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+            "add.rn.f32x2 pr, pa, pb;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+            : "=f"(r.x), "=f"(r.y)
+            : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+        return r;
+    }
+#endif
+    return cadd(a, b);
+}
+template <typename C> __host__ __device__ __forceinline__ C psub(C a, C b) {
+#if defined(__CUDA_ARCH__)
+    if constexpr (std::is_same<C, float2>::value) {
+        float2 r;
+        asm("{\n\t.reg .b64 pa, pb, pr;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+            "sub.rn.f32x2 pr, pa, pb;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+            : "=f"(r.x), "=f"(r.y)
+            : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+        return r;
+    }
+#endif
+    return csub(a, b);
+}
+// DIR i (a - b), formed directly in scalar: a rotated value would need its
+// halves swapped before a paired instruction could use it
+template <int DIR, typename C> __host__ __device__ __forceinline__ C rot_diff(C a, C b) {
+    return DIR > 0 ? cmk<C>(b.y - a.y, a.x - b.x) : cmk<C>(a.y - b.y, b.x - a.x);
+}
+
+// natural-order small DFTs; ROT2 returns DIR i X[2] in place of X[2]
 template <int DIR, typename C> __host__ __device__ __forceinline__ void rdft2(C* v) {
     C a = v[0], b = v[1];
-    v[0] = cadd(a, b);
-    v[1] = csub(a, b);
+    v[0] = padd(a, b);
+    v[1] = psub(a, b);
 }
-template <int DIR, typename C> __host__ __device__ __forceinline__ void rdft4(C* v) {
-    C t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-    C t2 = cadd(v[1], v[3]), t3 = mul_dir_i(csub(v[1], v[3]), DIR);
-    v[0] = cadd(t0, t2);
-    v[2] = csub(t0, t2);
-    v[1] = cadd(t1, t3);
-    v[3] = csub(t1, t3);
+template <int DIR, bool ROT2 = false, typename C> __host__ __device__ __forceinline__ void rdft4(C* v) {
+    C t0 = padd(v[0], v[2]), t1 = psub(v[0], v[2]);
+    C t2 = padd(v[1], v[3]), t3 = rot_diff<DIR>(v[1], v[3]);
+    v[0] = padd(t0, t2);
+    v[2] = ROT2 ? rot_diff<DIR>(t0, t2) : psub(t0, t2);
+    v[1] = padd(t1, t3);
+    v[3] = psub(t1, t3);
 }
 template <int DIR, typename C> __host__ __device__ __forceinline__ void rdft8(C* v) {
     using T = decltype(C{}.x);
@@ -83,7 +121,36 @@ template <int DIR, typename C> __host__ __device__ __forceinline__ void rdft8(C*
     C e[4] = {v[0], v[2], v[4], v[6]};
     C o[4] = {v[1], v[3], v[5], v[7]};
     rdft4<DIR>(e);
-    rdft4<DIR>(o);
+    rdft4<DIR, true>(o);   // o[2] comes back as DIR i O[2]
+    C w1o = cmk<C>(h * (o[1].x - DIR * o[1].y), h * (o[1].y + DIR * o[1].x));
+    C w3o = cmk<C>(-h * (o[3].x + DIR * o[3].y), h * (DIR * o[3].x - o[3].y));
+    v[0] = padd(e[0], o[0]);
+    v[4] = psub(e[0], o[0]);
+    v[1] = padd(e[1], w1o);
+    v[5] = psub(e[1], w1o);
+    v[2] = padd(e[2], o[2]);
+    v[6] = psub(e[2], o[2]);
+    v[3] = padd(e[3], w3o);
+    v[7] = psub(e[3], w3o);
+}
+// scalar 4- and 8-point DFTs of inputs whose upper half is zero: plain
+// arithmetic, so the compiler folds the zero operands away
+template <int DIR, typename C> __host__ __device__ __forceinline__ void rdft4_half(C* v) {
+    const C a = v[0], b = v[1];
+    const C ib = mul_dir_i(b, DIR);
+    v[0] = cadd(a, b);
+    v[2] = csub(a, b);
+    v[1] = cadd(a, ib);
+    v[3] = csub(a, ib);
+}
+template <int DIR, typename C> __host__ __device__ __forceinline__ void rdft8_half(C* v) {
+    using T = decltype(C{}.x);
+    const T h = (T)0.70710678118654752440084436210484904;
+    // X[k] = E[k] + w^k O[k] with E, O the 4-point DFTs of (v0, v2) and (v1, v3)
+    C e[4] = {v[0], v[2], cmk<C>(0, 0), cmk<C>(0, 0)};
+    C o[4] = {v[1], v[3], cmk<C>(0, 0), cmk<C>(0, 0)};
+    rdft4_half<DIR>(e);
+    rdft4_half<DIR>(o);
     C w1o = cmk<C>(h * (o[1].x - DIR * o[1].y), h * (o[1].y + DIR * o[1].x));
     C w2o = mul_dir_i(o[2], DIR);
     C w3o = cmk<C>(-h * (o[3].x + DIR * o[3].y), h * (DIR * o[3].x - o[3].y));
@@ -101,23 +168,29 @@ template <int DIR, typename C> __host__ __device__ __forceinline__ void rdft8(C*
 template <int N, int K, int DIR, bool HALF, typename C> __host__ __device__ __forceinline__ void dif_level(C* v) {
     if constexpr (K < N / 2) {
         using T = decltype(C{}.x);
-        C a = v[K];
-        C d;
+        const C a = v[K];
         if constexpr (HALF) {
-            d = a;
+            if constexpr (K == 0) {
+                v[K + N / 2] = a;
+            } else if constexpr (4 * K == N) {
+                v[K + N / 2] = mul_dir_i(a, DIR);
+            } else {
+                constexpr double c = cos2pi(K, N);
+                constexpr double s = DIR * sin2pi(K, N);
+                v[K + N / 2] = cmul(a, cmk<C>((T)c, (T)s));
+            }
         } else {
-            C b = v[K + N / 2];
-            v[K] = cadd(a, b);
-            d = csub(a, b);
-        }
-        if constexpr (K == 0) {
-            v[K + N / 2] = d;
-        } else if constexpr (4 * K == N) {
-            v[K + N / 2] = mul_dir_i(d, DIR);
-        } else {
-            constexpr double c = cos2pi(K, N);
-            constexpr double s = DIR * sin2pi(K, N);
-            v[K + N / 2] = cmul(d, cmk<C>((T)c, (T)s));
+            const C b = v[K + N / 2];
+            v[K] = padd(a, b);
+            if constexpr (K == 0) {
+                v[K + N / 2] = psub(a, b);
+            } else if constexpr (4 * K == N) {
+                v[K + N / 2] = rot_diff<DIR>(a, b);
+            } else {
+                constexpr double c = cos2pi(K, N);
+                constexpr double s = DIR * sin2pi(K, N);
+                v[K + N / 2] = cmul(psub(a, b), cmk<C>((T)c, (T)s));
+            }
         }
         dif_level<N, K + 1, DIR, HALF>(v);
     }
@@ -129,12 +202,11 @@ template <int N, int DIR, bool HALF, typename C> __host__ __device__ __forceinli
     } else if constexpr (N == 2) {
         if constexpr (HALF) v[1] = v[0];
         else rdft2<DIR>(v);
-    } else if constexpr (N == 4 || N == 8) {
-        if constexpr (HALF) {
-#pragma unroll
-            for (int i = N / 2; i < N; ++i) v[i] = cmk<C>(0, 0);
-        }
-        if constexpr (N == 4) rdft4<DIR>(v);
+    } else if constexpr (N == 4) {
+        if constexpr (HALF) rdft4_half<DIR>(v);
+        else rdft4<DIR>(v);
+    } else if constexpr (N == 8) {
+        if constexpr (HALF) rdft8_half<DIR>(v);
         else rdft8<DIR>(v);
     } else {
         dif_level<N, 0, DIR, HALF>(v);
