@@ -549,7 +549,7 @@ __global__ void __launch_bounds__(128, 7)
 }
 
 template <int L1, int L2>
-__global__ void __launch_bounds__(128, 8)
+__global__ void __launch_bounds__(128, (L1 * L2 >= 512) ? 6 : 8)
     k_xinv_reg(const float2* __restrict__ in, int Hs, float* __restrict__ out, long rows, float scale,
                const float2* __restrict__ twL, const float2* __restrict__ twP) {
     constexpr int L = L1 * L2, B = 4, NX = L;

@@ -243,3 +243,31 @@ def test_llg_step_autograd_against_central_differences():
             return float(torch.sum(w * LLGStep.apply(m0.detach() + e * v, Ms_t.detach(), ctx, 5e-14)))
     assert richardson(f, 1e-4) == pytest.approx(vdot(m0.grad, v), rel=1e-7)
     mm.mm_destroy(ctx)
+
+
+def test_design256_gradient_time_2000_steps(design256):
+    """Seconds per gradient on the 256 x 256 x 4 design mesh: 2000 RK4 steps
+    of 0.1 ps (0.2 ns) forward and the checkpointed adjoint, float32, with
+    the default sqrt(T) checkpoint interval; the gradient is finite and
+    non-zero.  The time is printed.  A 2-step gradient runs first: the
+    process's first autograd backward pays a one-time start-up of several
+    seconds that is not the adjoint's."""
+    import time
+    from paper_2606_01114_gb300.autograd import RK4Trajectory
+    w, Ms, m0 = design256
+    ctx = make_ctx(w["n"], w["d"], Ms, prec=mm.MM_F32)
+    m0d = dev(m0, mm.MM_F32)
+    warm = dev(Ms, mm.MM_F32).requires_grad_(True)
+    _loss(RK4Trajectory.apply(m0d, warm, ctx, 1e-13, 2, 0), 0.05).backward()
+    Ms_t = dev(Ms, mm.MM_F32).requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mN = RK4Trajectory.apply(m0d, Ms_t, ctx, 1e-13, 2000, 0)
+    t1 = time.perf_counter()
+    _loss(mN, 0.05).backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    g = Ms_t.grad
+    assert torch.isfinite(g).all() and float(g.abs().max()) > 0
+    print(f"design256 float32, 2000 RK4 steps: forward {t1 - t0:.2f} s, gradient (forward + adjoint) {t2 - t0:.2f} s")
+    mm.mm_destroy(ctx)
