@@ -51,8 +51,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["f32", "f64"], default="f32")
-    ap.add_argument("--fft-mode", choices=["fp32", "tf32", "bf16"], default="fp32",
-                    help="FP32 context only: tensor-core split-precision y passes")
+    ap.add_argument("--fft-mode", choices=["fp32", "tf32", "bf16", "ff"], default="fp32",
+                    help="tf32/bf16: tensor-core split-precision y passes (f32); ff: float-float demag passes (f64)")
     ap.add_argument("--workload", choices=["film512"], default="film512")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -97,7 +97,7 @@ def load_peaks():
 # the sources each timed kernel family is compiled from: stored ncu traffic
 # stays valid while these files are unchanged
 KERNEL_SOURCES = {
-    "demag": ("mm_demag.cu", "mm_fft.cuh", "mm_regfft.cuh", "mm_internal.cuh"),
+    "demag": ("mm_demag.cu", "mm_fft.cuh", "mm_regfft.cuh", "mm_ff.cuh", "mm_internal.cuh"),
     "stage": ("mm_llg.cu", "mm_fields.cuh", "mm_internal.cuh"),
 }
 FAMILY = {"xfwd": "demag", "yfwd": "demag", "zconv": "demag", "yinv": "demag", "xinv": "demag", "stage": "stage"}
@@ -394,7 +394,11 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     ctx = mm.mm_init_mesh(*n, *d, precision=prec, stream=stream)
     mm.mm_set_material(ctx, w["Ms"], w["A"], w["alpha"], w["Ku"])
-    if args.fft_mode != "fp32":
+    if args.fft_mode == "ff":
+        if prec != mm.MM_F64:
+            raise SystemExit("--fft-mode ff needs --precision f64")
+        mm.mm_set_fft_mode(ctx, mm.MM_FFT_FF)
+    elif args.fft_mode != "fp32":
         mm.mm_set_fft_mode(ctx, mm.MM_TC_TF32 if args.fft_mode == "tf32" else mm.MM_TC_BF16)
     m_host = wl.vortex(n, d, noise=0.05, seed=1)
     m = torch.tensor(m_host, dtype=tdtype, device="cuda")
@@ -460,8 +464,9 @@ def run_ours(args):
                 "frac": achieved / peak, "traffic": traffic, "peak_source": f"{peak_src} (hbm_gbs)",
                 "algorithmic_bytes_per_launch": algo}
     fl = algorithmic_flops(dom, n)
-    if prec == mm.MM_F64 and fl:
+    if prec == mm.MM_F64 and fl and args.fft_mode != "ff":
         # the FP64 path is bound by GB300's FP64 rate, far below its HBM roof
+        # (the float-float passes run on the FP32 pipes: HBM view)
         tf = fl / avg_s / 1e12
         roofline = {"bound": "alu", "kernel": dom, "achieved": tf, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
                     "frac": tf / FP64_TFLOPS, "traffic": traffic,
@@ -503,7 +508,7 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / max(accepted, 1), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision + ("/ff" if args.fft_mode == "ff" else ""), "data": "synthetic",
             "config": {"workload": "film512: 512x512x16 cells of 2 nm (padded FFT 1024x1024x32), Ms 8e5 A/m, "
                                    "A 1.3e-11 J/m, alpha 0.5, seeded vortex + 5% noise, adaptive RKF45 tol 1e-5 "
                                    "via relax()",

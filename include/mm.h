@@ -260,7 +260,7 @@ int mm_rk4_trajectory_vjp(mm_ctx* ctx, const void* m0, double dt, long nsteps, v
  * 5th-generation tensor cores, FP32 operands split into hi + lo parts of the
  * tensor-core type and multiplied as hi.hi + hi.lo + lo.hi with FP32
  * accumulation (about 21 significant bits for TF32, 16 for BF16). */
-enum { MM_TC_TF32 = 1, MM_TC_BF16 = 2 };
+enum { MM_TC_TF32 = 1, MM_TC_BF16 = 2, MM_FFT_FF = 3 };
 
 /* out[l][k] = sum_n in[l][n] exp(direction 2 pi i n k / 32) for nlines
  * lines of 32 complex FP32 values (interleaved re, im; device arrays,
@@ -269,10 +269,20 @@ enum { MM_TC_TF32 = 1, MM_TC_BF16 = 2 };
  * mm_last_error(NULL)). */
 int mm_dft32_tc(const void* in, void* out, long nlines, int mode, int direction, void* stream);
 
-/* FFT arithmetic of an MM_F32 context's demag passes: 0 = plain FP32
- * (default), MM_TC_TF32 or MM_TC_BF16 = the y passes of length 512 or 1024
- * run their 32-point level on tensor cores with split operands (the other
- * passes stay FP32).  INVALID_ARG for an MM_F64 context. */
+/* FFT arithmetic of a context's demag passes (Implementation section,
+ * Eq. 4: the convolution itself is unchanged, only the arithmetic that
+ * evaluates its transforms).  0 = the context's own precision (default).
+ * MM_F32 context: MM_TC_TF32 or MM_TC_BF16 = the y passes of length 512 or
+ * 1024 run their 32-point level on tensor cores with split operands (the
+ * other passes stay FP32).
+ * MM_F64 context: MM_FFT_FF = all five passes in float-float arithmetic
+ * (pairs of FP32 values, about 48 significant bits, on the FP32 pipes) while
+ * m, Ms, H and everything outside the demag passes stay float64; the padded
+ * sizes Px, Py, Pz must be powers of two.  Setting it allocates float-float
+ * copies of the Newell octant and twiddle tables (6 (Pz/2+1)(Py/2+1) Hs x 8
+ * bytes plus the tables), kept until mm_destroy.
+ * Errors: INVALID_ARG (unknown mode, mode not valid for the context's
+ * precision or mesh), NOMEM/CUDA (allocation or setup). */
 int mm_set_fft_mode(mm_ctx* ctx, int mode);
 
 /* MM_OK, or MM_ERR_TIMEOUT if a tensor-core wait of this device gave up

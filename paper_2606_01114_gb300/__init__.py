@@ -28,7 +28,7 @@ MM_ERR_DT_UNDERFLOW = -4
 MM_ERR_NOT_CONVERGED = -5
 MM_ERR_TIMEOUT = -6
 MM_ERR_NOMEM = -7
-MM_TC_TF32, MM_TC_BF16 = 1, 2
+MM_TC_TF32, MM_TC_BF16, MM_FFT_FF = 1, 2, 3
 # kernel classes for mm_kernel_time
 MM_K_XFWD, MM_K_YFWD, MM_K_ZCONV, MM_K_YINV, MM_K_XINV, MM_K_STAGE, MM_K_CONTROL, MM_K_REDUCE = range(8)
 MM_K_COUNT = 8
@@ -335,7 +335,9 @@ def mm_rk4_trajectory_vjp(ctx, m0, dt, nsteps, lam, gMs, checkpoint_every=0):
 
 
 def mm_set_fft_mode(ctx, mode):
-    """0 = plain FP32 passes, MM_TC_TF32 / MM_TC_BF16 = tensor-core y passes."""
+    """0 = the context's own precision; MM_TC_TF32 / MM_TC_BF16 = tensor-core
+    y passes (MM_F32 context); MM_FFT_FF = float-float demag passes (MM_F64
+    context, power-of-two padded sizes)."""
     _check(ctx, _load().mm_set_fft_mode(ctx.handle, int(mode)))
 
 

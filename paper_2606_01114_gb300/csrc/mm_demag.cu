@@ -23,12 +23,29 @@
 #include <vector>
 
 #include "mm_fft.cuh"
+#include "mm_ff.cuh"
 #include "mm_regfft.cuh"
 
 namespace mm {
 namespace {
 
 template <typename T> using C_t = typename cx<T>::type;
+
+// Loads and stores at the real-array boundary of the passes: S is the type
+// the caller's arrays hold (m, Ms, H), T the arithmetic of the passes (the
+// same type, or float-float over double arrays).
+template <typename C, typename S> __device__ __forceinline__ C ld_c(const S* p, long j) {
+    if constexpr (std::is_same<C, C_t<S>>::value) return reinterpret_cast<const C*>(p)[j];
+    else return from_d2<C>(reinterpret_cast<const C_t<S>*>(p)[j]);
+}
+template <typename C, typename S> __device__ __forceinline__ void st_c(S* p, long j, C v) {
+    if constexpr (std::is_same<C, C_t<S>>::value) reinterpret_cast<C*>(p)[j] = v;
+    else reinterpret_cast<C_t<S>*>(p)[j] = cmk<C_t<S>>(to_d(v.x), to_d(v.y));
+}
+template <typename T, typename S> __device__ __forceinline__ T ld_r(S v) {
+    if constexpr (std::is_same<T, S>::value) return v;
+    else return from_real<T>(v);
+}
 
 // ------------------------------------------------------------------ K2
 // Real rows -> packed complex FFT -> Hx frequencies.
@@ -37,8 +54,8 @@ template <typename T> using C_t = typename cx<T>::type;
 //   or nullptr (scalar ms).  Complex length L = 2^lgL = Px / 2.
 //   Shared memory: B lines of L (FftGeom layout); global accesses run with
 //   the row index b fastest across a warp (B row segments per instruction).
-template <typename T>
-__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_xfwd(const T* __restrict__ in, long in_ld, int nin, const T* __restrict__ Ms, T ms,
+template <typename T, typename S = T>
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_xfwd(const S* __restrict__ in, long in_ld, int nin, const S* __restrict__ Ms, T ms,
                        long ms_rows, C_t<T>* __restrict__ out, int Hs, int lgL, long rows, int lgB,
                        const C_t<T>* __restrict__ twL, const C_t<T>* __restrict__ twP) {
     using C = C_t<T>;
@@ -59,9 +76,9 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_xfwd(const T* _
             long r = r0 + b;
             v[u] = cmk<C>(0, 0);
             if (idx < total && j < npair && r < rows) {
-                v[u] = reinterpret_cast<const C*>(in + r * in_ld)[j];
+                v[u] = ld_c<C>(in + r * in_ld, j);
                 if (Ms) {
-                    C w = reinterpret_cast<const C*>(Ms + (r % ms_rows) * in_ld)[j];
+                    C w = ld_c<C>(Ms + (r % ms_rows) * in_ld, j);
                     v[u].x *= w.x;
                     v[u].y *= w.y;
                 } else {
@@ -94,19 +111,19 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_xfwd(const T* _
 }
 
 // nx == 1: no x transform, M copied into the complex array.
-template <typename T>
-__global__ void k_x1fwd(const T* __restrict__ in, const T* __restrict__ Ms, T ms, long ms_rows,
+template <typename T, typename S = T>
+__global__ void k_x1fwd(const S* __restrict__ in, const S* __restrict__ Ms, T ms, long ms_rows,
                         C_t<T>* __restrict__ out, int Hs, long rows) {
     long r = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= rows) return;
-    T w = Ms ? Ms[r % ms_rows] : ms;
-    out[r * Hs] = cmk<C_t<T>>(in[r] * w, (T)0);
+    T w = Ms ? ld_r<T>(Ms[r % ms_rows]) : ms;
+    out[r * Hs] = cmk<C_t<T>>(ld_r<T>(in[r]) * w, (T)0);
 }
 
 // ------------------------------------------------------------------ K6
 // Hx frequencies -> inverse packed complex FFT -> nx real outputs, scaled.
-template <typename T>
-__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_xinv(const C_t<T>* __restrict__ in, int Hs, T* __restrict__ out, int nx, int lgL, long rows,
+template <typename T, typename S = T>
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_xinv(const C_t<T>* __restrict__ in, int Hs, S* __restrict__ out, int nx, int lgL, long rows,
                        int lgB, T scale, const C_t<T>* __restrict__ twL, const C_t<T>* __restrict__ twP) {
     using C = C_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -149,15 +166,15 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_xinv(const C_t<
         long r = r0 + b;
         if (r >= rows) continue;
         C z = s[sidx(g, 0, j, b)];
-        reinterpret_cast<C*>(out + r * (long)nx)[j] = cmk<C>(z.x * scale, z.y * scale);
+        st_c(out + r * (long)nx, j, cmk<C>(z.x * scale, z.y * scale));
     }
 }
 
-template <typename T>
-__global__ void k_x1inv(const C_t<T>* __restrict__ in, int Hs, T* __restrict__ out, long rows, T scale) {
+template <typename T, typename S = T>
+__global__ void k_x1inv(const C_t<T>* __restrict__ in, int Hs, S* __restrict__ out, long rows, T scale) {
     long r = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= rows) return;
-    out[r] = in[r * Hs].x * scale;
+    out[r] = to_d(in[r * Hs].x * scale);
 }
 
 // ----------------------------------------------------------- K3 / K5
@@ -1067,19 +1084,125 @@ int setup(mm_ctx* ctx) {
     return rc;
 }
 
+// FP64 context, float-float arithmetic (MM_FFT_FF): the generic passes
+// with ff in place of double.  m, Ms and H stay double; the spectra in bufA
+// and bufB hold ffc (16 bytes, like double2); the octant and twiddles come
+// from their float-float copies (ctx->kern_ff, ctx->tw.ff).  Power-of-two
+// Px, Py, Pz only (checked when the mode is set).
+int apply_ff(mm_ctx* ctx, const double* m, double* H, bool unit) {
+    using C = ffc;
+    const long rows = 3L * ctx->nz * ctx->ny;
+    C* A = (C*)ctx->bufA;
+    C* Bf = (C*)ctx->bufB;
+    C* xout = ctx->Py == 1 ? Bf : A;
+    const double* Ms = (ctx->has_Ms_cell && !unit) ? (const double*)ctx->Ms_cell : nullptr;
+    const ff ms = unit ? ff(1) : ff(ctx->Ms);
+    const long ms_rows = (long)ctx->nz * ctx->ny;
+    const C* tw = (const C*)ctx->tw.ff;
+    int rc;
+    {   // K2
+        KernelTimer kt(ctx, MM_K_XFWD);
+        if (ctx->Px == 1) {
+            k_x1fwd<ff, double><<<(unsigned)((rows + 255) / 256), 256, 0, ctx->stream>>>(m, Ms, ms, ms_rows, xout,
+                                                                                      ctx->Hs, rows);
+        } else {
+            const int L = ctx->Px / 2;
+            const int B = x_rows_per_block(L);
+            const size_t smem = (size_t)L * B * sizeof(C);
+            if ((rc = set_smem(ctx, (const void*)k_xfwd<ff, double>, smem))) return rc;
+            k_xfwd<ff, double><<<(unsigned)((rows + B - 1) / B), block_threads(B * L / 8), smem, ctx->stream>>>(
+                m, ctx->nx, ctx->nx, Ms, ms, ms_rows, xout, ctx->Hs, ilog2(L), rows, ilog2(B), tw + ctx->tw.off_lx,
+                tw + ctx->tw.off_px);
+        }
+        MM_LAUNCH_CHECK(ctx);
+    }
+    // K3
+    if (ctx->Py > 1) {
+        ColGeom g{ctx->Hs, ctx->Hs, 3 * ctx->nz, (long)ctx->ny * ctx->Hs, 0, (long)ctx->Py * ctx->Hs, 0};
+        if ((rc = run_cols<ff, -1>(ctx, A, Bf, ctx->Py, ctx->ny, ctx->Py, 3 * ctx->nz, g, tw + ctx->tw.off_py)))
+            return rc;
+    }
+    {   // K4
+        KernelTimer kt(ctx, MM_K_ZCONV);
+        const int Pz = ctx->Pz;
+        const int B = z_tile(Pz, sizeof(C));
+        const size_t smem = (size_t)3 * Pz * B * sizeof(C) + (size_t)6 * ctx->Pz2 * B * sizeof(ff);
+        if ((rc = set_smem(ctx, (const void*)k_zconv<ff>, smem))) return rc;
+        dim3 grid((unsigned)((ctx->Hx + B - 1) / B), (unsigned)(ctx->Py / 2 + 1));
+        k_zconv<ff><<<grid, block_threads(3 * B * Pz / 8), smem, ctx->stream>>>(
+            Bf, (const ff*)ctx->kern_ff, ctx->nz, ilog2(Pz), ctx->Py, ctx->Hs, ctx->Hx, ctx->Py2, ctx->Pz2, ilog2(B),
+            tw + ctx->tw.off_pz);
+        MM_LAUNCH_CHECK(ctx);
+    }
+    // K5
+    if (ctx->Py > 1) {
+        ColGeom g{ctx->Hs, ctx->Hs, 3 * ctx->nz, (long)ctx->Py * ctx->Hs, 0, (long)ctx->ny * ctx->Hs, 0};
+        if ((rc = run_cols<ff, +1>(ctx, Bf, A, ctx->Py, ctx->Py, ctx->ny, 3 * ctx->nz, g, tw + ctx->tw.off_py)))
+            return rc;
+    }
+    {   // K6
+        const C* xin = ctx->Py == 1 ? Bf : A;
+        const ff scale = ff(1.0 / ((double)ctx->Lx * ctx->Py * ctx->Pz));
+        KernelTimer kt(ctx, MM_K_XINV);
+        if (ctx->Px == 1) {
+            k_x1inv<ff, double><<<(unsigned)((rows + 255) / 256), 256, 0, ctx->stream>>>(xin, ctx->Hs, H, rows, scale);
+        } else {
+            const int L = ctx->Lx;
+            const int B = x_rows_per_block(L);
+            const size_t smem = (size_t)L * B * sizeof(C);
+            if ((rc = set_smem(ctx, (const void*)k_xinv<ff, double>, smem))) return rc;
+            k_xinv<ff, double><<<(unsigned)((rows + B - 1) / B), block_threads(B * L / 8), smem, ctx->stream>>>(
+                xin, ctx->Hs, H, ctx->nx, ilog2(L), rows, ilog2(B), scale, tw + ctx->tw.off_lx, tw + ctx->tw.off_px);
+        }
+        MM_LAUNCH_CHECK(ctx);
+    }
+    return MM_OK;
+}
+
+// float-float copy of an array of doubles (rounding split, once per mode switch)
+__global__ void k_split_ff(const double* __restrict__ in, ff* __restrict__ out, long n) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double d = in[i];
+    const float h = __double2float_rn(d);
+    out[i] = ff(h, __double2float_rn(d - (double)h));
+}
+
 }  // namespace
+
+// Prepares MM_FFT_FF on an FP64 context: float-float copies of the octant
+// and of the twiddle tables (kept until the context is destroyed).
+int demag_prepare_ff(mm_ctx* ctx) {
+    if (ctx->kern_ff && ctx->tw.ff) return MM_OK;
+    const long nk = 6L * ctx->Pz2 * ctx->Py2 * ctx->Hs;
+    const long nt = 2L * (ctx->tw.off_pz + ctx->Pz);          // doubles in the twiddle table
+    if (!ctx->kern_ff) MM_CUDA_CHECK(ctx, cudaMalloc(&ctx->kern_ff, nk * sizeof(ff)));
+    if (!ctx->tw.ff) MM_CUDA_CHECK(ctx, cudaMalloc(&ctx->tw.ff, nt * sizeof(ff)));
+    k_split_ff<<<(unsigned)((nk + 255) / 256), 256, 0, ctx->stream>>>((const double*)ctx->kern, (ff*)ctx->kern_ff, nk);
+    MM_LAUNCH_CHECK(ctx);
+    k_split_ff<<<(unsigned)((nt + 255) / 256), 256, 0, ctx->stream>>>((const double*)ctx->tw.f64, (ff*)ctx->tw.ff, nt);
+    MM_LAUNCH_CHECK(ctx);
+    MM_CUDA_CHECK(ctx, cudaStreamSynchronize(ctx->stream));
+    return MM_OK;
+}
 
 int demag_setup(mm_ctx* ctx) {
     return ctx->prec == MM_F64 ? setup<double>(ctx) : setup<float>(ctx);
 }
 
 int demag_apply(mm_ctx* ctx, const void* m, void* H) {
-    if (ctx->prec == MM_F64) return apply<double>(ctx, (const double*)m, (double*)H);
+    if (ctx->prec == MM_F64) {
+        if (ctx->fft_mode == MM_FFT_FF) return apply_ff(ctx, (const double*)m, (double*)H, false);
+        return apply<double>(ctx, (const double*)m, (double*)H);
+    }
     return apply<float>(ctx, (const float*)m, (float*)H);
 }
 
 int demag_apply_unit(mm_ctx* ctx, const void* g, void* H) {
-    if (ctx->prec == MM_F64) return apply<double>(ctx, (const double*)g, (double*)H, true);
+    if (ctx->prec == MM_F64) {
+        if (ctx->fft_mode == MM_FFT_FF) return apply_ff(ctx, (const double*)g, (double*)H, true);
+        return apply<double>(ctx, (const double*)g, (double*)H, true);
+    }
     return apply<float>(ctx, (const float*)g, (float*)H, true);
 }
 

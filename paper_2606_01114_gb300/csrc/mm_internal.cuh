@@ -60,6 +60,7 @@ struct Tables {
     // exp(-2 pi i m / L), m in [0, L), for L in {Lx, Px, Py, Pz}
     void* f64 = nullptr;   // double2
     void* f32 = nullptr;   // float2 (only for MM_F32 contexts)
+    void* ff = nullptr;    // float-float copy of f64 (MM_FFT_FF on an MM_F64 context)
     long off_lx = 0, off_px = 0, off_py = 0, off_pz = 0;
 };
 
@@ -77,7 +78,8 @@ struct mm_ctx {
     int Hx;                   // kept x frequencies (nx + 1, or 1)
     int Hs;                   // row stride of k-space arrays (Hx rounded up to 16)
     int Py2, Pz2;             // Py/2+1, Pz/2+1: stored kernel octant extents
-    int fft_mode;             // 0 plain FP32 passes, MM_TC_TF32 / MM_TC_BF16: tensor-core y passes
+    int fft_mode;             // 0 plain passes, MM_TC_TF32 / MM_TC_BF16: tensor-core y passes (FP32),
+                              // MM_FFT_FF: float-float passes (FP64)
     mm_fno* stage_surrogate;  // set inside mm_relax_surrogate while a window uses the surrogate
     long surrogate_evals, exact_evals;   // demag evaluations of either kind (surrogate relax statistics)
 
@@ -94,6 +96,7 @@ struct mm_ctx {
 
     // buffers (path precision T; complex = 2T)
     void* kern;               // [6][Pz2][Py2][Hs] real k-space Newell octant
+    void* kern_ff;            // float-float copy of kern (MM_FFT_FF), or NULL
     void* bufA;               // complex [3][nz][ny][Hs]
     void* bufB;               // complex [3][nz][Py][Hs]
     void* Hd;                 // [3][N] demag field of the current stage state
@@ -181,6 +184,7 @@ int tc_prepare(mm_ctx* ctx);
 int demag_setup(mm_ctx* ctx);                          // K1: Newell tensor -> k-space octant
 int demag_apply(mm_ctx* ctx, const void* m, void* H);  // K2..K6
 int demag_apply_unit(mm_ctx* ctx, const void* g, void* H);  // same with Ms = 1 (adjoint)
+int demag_prepare_ff(mm_ctx* ctx);                     // float-float tables for MM_FFT_FF
 // surrogate network: its grid, and the stream its launches go to (returns the old one)
 void fno_grid(const mm_fno* f, int* nx, int* ny);
 cudaStream_t fno_swap_stream(mm_fno* f, cudaStream_t s);

@@ -515,7 +515,19 @@ using namespace mm;
 
 extern "C" int mm_set_fft_mode(mm_ctx* ctx, int mode) {
     if (!ctx) return fail(nullptr, MM_ERR_INVALID_ARG, "ctx is NULL");
-    if (mode != 0 && mode != MM_TC_TF32 && mode != MM_TC_BF16) return fail(ctx, MM_ERR_INVALID_ARG, "bad FFT mode %d", mode);
+    if (mode != 0 && mode != MM_TC_TF32 && mode != MM_TC_BF16 && mode != MM_FFT_FF)
+        return fail(ctx, MM_ERR_INVALID_ARG, "bad FFT mode %d", mode);
+    if (mode == MM_FFT_FF) {
+        auto p2 = [](int n) { return n > 0 && (n & (n - 1)) == 0; };
+        if (ctx->prec != MM_F64) return fail(ctx, MM_ERR_INVALID_ARG, "float-float passes need an MM_F64 context");
+        if (!p2(ctx->Px) || !p2(ctx->Py) || !p2(ctx->Pz))
+            return fail(ctx, MM_ERR_INVALID_ARG, "float-float passes need power-of-two padded sizes (nx, ny, nz)");
+        MM_BIND(ctx);
+        int rc = demag_prepare_ff(ctx);
+        if (rc) return rc;
+        ctx->fft_mode = mode;
+        return MM_OK;
+    }
     if (mode != 0 && ctx->prec != MM_F32) return fail(ctx, MM_ERR_INVALID_ARG, "tensor-core passes need an MM_F32 context");
     MM_BIND(ctx);
     if (mode != 0) {

@@ -1,0 +1,158 @@
+"""GPU parity of the float-float demag passes (MM_FFT_FF on an MM_F64
+context) against the float64 CPU oracle, at the float64 path's tolerance
+(relative L2 1e-12 per field): demag on the power-of-two meshes of the main
+parity suite, per-cell Ms with vacuum, a 128 x 128 x 16 film, RK4 steps
+checked one by one, the transpose (dot-product) test of the adjoint, and the
+mode's error paths."""
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import micromag
+
+torch = pytest.importorskip("torch")
+import paper_2606_01114_gb300 as mm  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2606_01114_gb300 import build
+    build.build()
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def ff_ctx(p, mode=mm.MM_FFT_FF):
+    nx, ny, nz = p.n
+    ctx = mm.mm_init_mesh(nx, ny, nz, *p.d, precision=mm.MM_F64)
+    uniform = np.all(p.Ms == p.Ms.flat[0])
+    mm.mm_set_material(ctx, float(p.Ms.flat[0]) if uniform else 8e5, float(p.A.flat[0]), p.alpha, p.Ku, tuple(p.u))
+    mm.mm_set_external_field(ctx, *p.h_ext)
+    if not uniform:
+        mm.mm_set_material_fields(ctx, dev(p.Ms))
+    mm.mm_set_fft_mode(ctx, mode)
+    return ctx
+
+
+MESHES = [
+    ((8, 4, 2), (2.5e-9, 2.5e-9, 3e-9)),
+    ((16, 8, 1), (2e-9, 2e-9, 2e-9)),
+    ((1, 8, 4), (2e-9, 1e-9, 3e-9)),
+    ((4, 1, 1), (1e-9, 1e-9, 1e-9)),
+    ((32, 16, 8), (2e-9, 2e-9, 2e-9)),
+    ((64, 64, 4), (2.5e-9, 2.5e-9, 3e-9)),
+    ((128, 128, 16), (2e-9, 2e-9, 2e-9)),
+]
+
+
+@pytest.mark.parametrize("n,d", MESHES)
+def test_ff_demag_matches_oracle(n, d):
+    p = micromag.Problem(n, d)
+    m = wl.random_unit(n, seed=0)
+    ctx = ff_ctx(p)
+    H = torch.empty(ctx.shape3, dtype=torch.float64, device="cuda")
+    mm.mm_demag_field(ctx, dev(m), H)
+    err = rel_l2(host(H), p.demag_fft(m))
+    assert err < TOL, err
+    mm.mm_destroy(ctx)
+
+
+def test_ff_demag_per_cell_ms_with_vacuum():
+    n, d = (32, 16, 4), (2e-9, 3e-9, 1.5e-9)
+    Ms = wl.smooth_field(n, 4e5, 9e5, sigma_cells=3.0, seed=5)
+    Ms[:, :4, :5] = 0.0
+    p = micromag.Problem(n, d, Ms_cell=Ms)
+    m = wl.random_unit(n, seed=1)
+    ctx = ff_ctx(p)
+    H = torch.empty(ctx.shape3, dtype=torch.float64, device="cuda")
+    mm.mm_demag_field(ctx, dev(m), H)
+    assert rel_l2(host(H), p.demag_fft(m)) < TOL
+    mm.mm_destroy(ctx)
+
+
+def test_ff_rk4_steps_film64():
+    """64 x 64 x 4 film, random m, 20 RK4 steps at 1e-13 s: each GPU step
+    against the oracle's step from the GPU's previous state (1e-12), and
+    |m| = 1 after every step."""
+    w = wl.WORKLOADS["film64"]
+    p = micromag.Problem(w["n"], w["d"], Ms=w["Ms"], A=w["A"], alpha=w["alpha"])
+    m = wl.random_unit(w["n"], seed=0)
+    ctx = ff_ctx(p)
+    md = dev(m)
+    t = 0.0
+    prev = m
+    for _ in range(20):
+        t, _, _ = mm.mm_llg_step(ctx, md, t, 1e-13, mm.MM_RK4)
+        cur = host(md)
+        assert rel_l2(cur, p.rk4_step(prev, 1e-13)) < TOL
+        assert np.max(np.abs(np.linalg.norm(cur, axis=0) - 1)) < 1e-14
+        prev = cur
+    mm.mm_destroy(ctx)
+
+
+def test_ff_demag_transpose_dot_product():
+    """Demag with the symmetric Newell tensor is self-adjoint:
+    <g, H(v)> = <H(g), v> through the adjoint entry point, to 1e-12."""
+    n, d = (16, 8, 4), (2.5e-9, 2.5e-9, 3e-9)
+    Ms = wl.smooth_field(n, 4e5, 9e5, sigma_cells=2.0, seed=1)
+    p = micromag.Problem(n, d, Ms_cell=Ms)
+    ctx = ff_ctx(p)
+    rng = np.random.default_rng(2)
+    v = dev(rng.standard_normal(ctx.shape3))
+    g = dev(rng.standard_normal(ctx.shape3))
+    Hv = torch.empty_like(v)
+    mm.mm_demag_field(ctx, v, Hv)
+    gm = torch.empty_like(v)
+    gMs = torch.zeros(ctx.shape1, dtype=torch.float64, device="cuda")
+    mm.mm_demag_vjp(ctx, g, v, gm, gMs)
+    a, b = float(torch.sum(g * Hv)), float(torch.sum(gm * v))
+    assert a == pytest.approx(b, rel=1e-12)
+    mm.mm_destroy(ctx)
+
+
+def test_ff_mode_switches_back_to_native():
+    """Mode 0 after MM_FFT_FF gives the native float64 field again, and both
+    agree with the oracle."""
+    n, d = (32, 16, 8), (2e-9, 2e-9, 2e-9)
+    p = micromag.Problem(n, d)
+    m = dev(wl.random_unit(n, seed=3))
+    ctx = ff_ctx(p)
+    H_ff = torch.empty_like(m)
+    mm.mm_demag_field(ctx, m, H_ff)
+    mm.mm_set_fft_mode(ctx, 0)
+    H_64 = torch.empty_like(m)
+    mm.mm_demag_field(ctx, m, H_64)
+    ref = p.demag_fft(host(m))
+    assert rel_l2(host(H_ff), ref) < TOL
+    assert rel_l2(host(H_64), ref) < TOL
+    assert not torch.equal(H_ff, H_64)          # the two arithmetics really differ
+    mm.mm_destroy(ctx)
+
+
+def test_ff_mode_errors():
+    ctx = mm.mm_init_mesh(8, 8, 2, 1e-9, 1e-9, 1e-9, precision=mm.MM_F32)
+    with pytest.raises(mm.MMError) as e:
+        mm.mm_set_fft_mode(ctx, mm.MM_FFT_FF)
+    assert e.value.code == mm.MM_ERR_INVALID_ARG
+    mm.mm_destroy(ctx)
+    ctx = mm.mm_init_mesh(100, 25, 1, 5e-9, 5e-9, 3e-9, precision=mm.MM_F64)   # Px = 200
+    with pytest.raises(mm.MMError) as e:
+        mm.mm_set_fft_mode(ctx, mm.MM_FFT_FF)
+    assert e.value.code == mm.MM_ERR_INVALID_ARG
+    mm.mm_destroy(ctx)
