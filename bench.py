@@ -98,7 +98,7 @@ def load_peaks():
 # stays valid while these files are unchanged
 KERNEL_SOURCES = {
     "demag": ("mm_demag.cu", "mm_fft.cuh", "mm_regfft.cuh", "mm_ff.cuh", "mm_internal.cuh"),
-    "stage": ("mm_llg.cu", "mm_fields.cuh", "mm_internal.cuh"),
+    "stage": ("mm_llg.cu", "mm_fields.cuh", "mm_ff.cuh", "mm_internal.cuh"),
 }
 FAMILY = {"xfwd": "demag", "yfwd": "demag", "zconv": "demag", "yinv": "demag", "xinv": "demag", "stage": "stage"}
 # kernel-name prefixes of each timed class as ncu reports them

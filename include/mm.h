@@ -276,9 +276,11 @@ int mm_dft32_tc(const void* in, void* out, long nlines, int mode, int direction,
  * 1024 run their 32-point level on tensor cores with split operands (the
  * other passes stay FP32).
  * MM_F64 context: MM_FFT_FF = all five passes in float-float arithmetic
- * (pairs of FP32 values, about 48 significant bits, on the FP32 pipes) while
- * m, Ms, H and everything outside the demag passes stay float64; the padded
- * sizes Px, Py, Pz must be powers of two.  Setting it allocates float-float
+ * (pairs of FP32 values, about 48 significant bits, on the FP32 pipes), and,
+ * for uniform Ms and A without DMI or STT, the LLG stage kernel as well
+ * (its renormalisation finished in float64); m, Ms, H, the stage slopes and
+ * everything else stay float64 arrays; the padded sizes Px, Py, Pz must be
+ * powers of two.  Setting it allocates float-float
  * copies of the Newell octant and twiddle tables (6 (Pz/2+1)(Py/2+1) Hs x 8
  * bytes plus the tables), kept until mm_destroy.
  * Errors: INVALID_ARG (unknown mode, mode not valid for the context's

@@ -17,6 +17,7 @@
 // synchronisation.  Energies and the torque maximum (K9) accumulate in FP64.
 #include <cmath>
 
+#include "mm_ff.cuh"
 #include "mm_fields.cuh"
 
 namespace mm {
@@ -376,6 +377,147 @@ __global__ void __launch_bounds__(256) k_stage4(Params<float> p, float wx, float
     if constexpr (LAST && METHOD == MM_RKF45) block_max_atomic(err, &ctl->err_bits);
 }
 
+// K7 in float-float arithmetic (MM_FFT_FF on an FP64 context), uniform
+// material, no DMI or STT: the same per-cell arithmetic as k_stage on
+// (h + l) float pairs (mm_ff.cuh), so the FP64 step runs on the FP32 pipes.
+// Every array stays float64 (each value converted on load and on store); the
+// RKF45 error is reduced as the squared norm per block, with one square root
+// per block; the renormalisation uses a float-float Newton inverse square
+// root started from rsqrtf.
+struct KPtrsD {
+    double* k[6];
+};
+struct FFStageCoef {
+    ff wx, wy, wz;     // A (2 / (mu0 d^2)) / Ms per axis
+    ff anis;           // 2 Ku / (mu0 Ms)
+    ff ux, uy, uz, hx, hy, hz;
+    ff pref, alpha;    // -gamma / (1 + alpha^2), alpha
+};
+
+__device__ __forceinline__ V3<ff> ld3ff(const double* __restrict__ a, long i, long N) {
+    return {d2ff(a[i]), d2ff(a[i + N]), d2ff(a[i + 2 * N])};
+}
+__device__ __forceinline__ void st3ff(double* __restrict__ a, long i, long N, const V3<ff>& v) {
+    a[i] = ff2d(v.x);
+    a[i + N] = ff2d(v.y);
+    a[i + 2 * N] = ff2d(v.z);
+}
+__device__ __forceinline__ ff half_of(ff a) { return ff(0.5f * a.h, 0.5f * a.l); }   // exact
+
+template <int METHOD, int S>
+__global__ void __launch_bounds__(256)
+    k_stage_ff(FFStageCoef c, int nx, int ny, int nz, long N, const double* __restrict__ m_in,
+               const double* __restrict__ Hd, const double* m0, KPtrsD kb, double* m_out, Control* ctl) {
+    constexpr int NS = rk_stages(METHOD);
+    constexpr bool LAST = (S == NS - 1);
+    if (ctl->status != 0 || ctl->done) return;
+    const ff dt = d2ff(ctl->dt);
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    double w2 = 0.0;   // squared error norm of this cell (RKF45 last stage)
+    if (i < N) {
+        int x, y, z;
+        decompose(i, nx, ny, x, y, z);
+        const V3<ff> mi = ld3ff(m_in, i, N);
+        // exchange (Eq. 2): sum over present neighbours w_axis (m_nb - m_i)
+        V3<ff> h = {ff(0), ff(0), ff(0)};
+        auto nb = [&](long j, ff w) {
+            h.x += w * (d2ff(m_in[j]) - mi.x);
+            h.y += w * (d2ff(m_in[j + N]) - mi.y);
+            h.z += w * (d2ff(m_in[j + 2 * N]) - mi.z);
+        };
+        const long sy = nx, sz = (long)nx * ny;
+        if (x > 0) nb(i - 1, c.wx);
+        if (x < nx - 1) nb(i + 1, c.wx);
+        if (y > 0) nb(i - sy, c.wy);
+        if (y < ny - 1) nb(i + sy, c.wy);
+        if (z > 0) nb(i - sz, c.wz);
+        if (z < nz - 1) nb(i + sz, c.wz);
+        // anisotropy, Zeeman, demag
+        const ff k = c.anis * (mi.x * c.ux + mi.y * c.uy + mi.z * c.uz);
+        const V3<ff> d = ld3ff(Hd, i, N);
+        h = {h.x + (k * c.ux + c.hx) + d.x, h.y + (k * c.uy + c.hy) + d.y, h.z + (k * c.uz + c.hz) + d.z};
+        // LLG right-hand side (Eq. 1)
+        const V3<ff> a = {mi.y * h.z - mi.z * h.y, mi.z * h.x - mi.x * h.z, mi.x * h.y - mi.y * h.x};
+        const V3<ff> b = {mi.y * a.z - mi.z * a.y, mi.z * a.x - mi.x * a.z, mi.x * a.y - mi.y * a.x};
+        const V3<ff> ks = {c.pref * (a.x + c.alpha * b.x), c.pref * (a.y + c.alpha * b.y),
+                           c.pref * (a.z + c.alpha * b.z)};
+        const V3<ff> a0 = S == 0 ? mi : ld3ff(m0, i, N);
+        if constexpr (!LAST) {
+            V3<ff> acc = {ff(0), ff(0), ff(0)};
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+                const double cj = rk_a(METHOD, S + 1, j);
+                if (cj != 0.0) {
+                    const ff cf = ff(cj);
+                    const V3<ff> kj = ld3ff(kb.k[j], i, N);
+                    acc = {acc.x + cf * kj.x, acc.y + cf * kj.y, acc.z + cf * kj.z};
+                }
+            }
+            const ff cs = ff(rk_a(METHOD, S + 1, S));
+            acc = {acc.x + cs * ks.x, acc.y + cs * ks.y, acc.z + cs * ks.z};
+            st3ff(kb.k[S], i, N, ks);
+            st3ff(m_out, i, N, V3<ff>{a0.x + dt * acc.x, a0.y + dt * acc.y, a0.z + dt * acc.z});
+        } else {
+            V3<ff> acc = {ff(0), ff(0), ff(0)}, e = {ff(0), ff(0), ff(0)};
+#pragma unroll
+            for (int j = 0; j < NS; ++j) {
+                const double cb = rk_b(METHOD, j), ce = rk_e(METHOD, j);
+                if (cb != 0.0 || ce != 0.0) {
+                    const V3<ff> kj = j == S ? ks : ld3ff(kb.k[j], i, N);
+                    const ff fb = ff(cb), fe = ff(ce);
+                    acc = {acc.x + fb * kj.x, acc.y + fb * kj.y, acc.z + fb * kj.z};
+                    e = {e.x + fe * kj.x, e.y + fe * kj.y, e.z + fe * kj.z};
+                }
+            }
+            V3<ff> mn = {a0.x + dt * acc.x, a0.y + dt * acc.y, a0.z + dt * acc.z};
+            const ff n2 = mn.x * mn.x + mn.y * mn.y + mn.z * mn.z;
+            if (n2.h > 0.f && isfinite(n2.h)) {
+                // y = 1 / sqrt(n2): rsqrtf start, two Newton steps y <- y (3/2 - n2 y^2 / 2)
+                ff yv = ff(rsqrtf(n2.h));
+                yv = yv * (ff(1.5) - half_of(n2 * (yv * yv)));
+                yv = yv * (ff(1.5) - half_of(n2 * (yv * yv)));
+                mn = {mn.x * yv, mn.y * yv, mn.z * yv};
+            }
+            const bool bad = !(isfinite(mn.x.h) && isfinite(mn.y.h) && isfinite(mn.z.h));
+            if (METHOD == MM_RKF45) {
+                w2 = ff2d(e.x * e.x + e.y * e.y + e.z * e.z);
+                if (bad || !isfinite(w2)) w2 = INFINITY;
+            } else if (bad) {
+                atomicCAS(&ctl->status, 0, (int)MM_ERR_NONFINITE);
+            }
+            // |m| - 1 is now a few float-float units (~1e-14); one first-order
+            // correction m (3/2 - |m|^2 / 2) in float64 leaves O(1e-28)
+            double ox = ff2d(mn.x), oy = ff2d(mn.y), oz = ff2d(mn.z);
+            if (!bad) {
+                const double f = 1.5 - 0.5 * (ox * ox + oy * oy + oz * oz);
+                ox *= f;
+                oy *= f;
+                oz *= f;
+            }
+            m_out[i] = ox;
+            m_out[i + N] = oy;
+            m_out[i + 2 * N] = oz;
+        }
+    }
+    if constexpr (LAST && METHOD == MM_RKF45) {
+        // block max of the squared norms; err = dt sqrt(max) for the controller
+        __shared__ double red[32];
+        for (int o = 16; o > 0; o >>= 1) w2 = fmax(w2, __shfl_xor_sync(0xffffffffu, w2, o));
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        if (lane == 0) red[w] = w2;
+        __syncthreads();
+        if (w == 0) {
+            const int nw = (blockDim.x + 31) >> 5;
+            w2 = lane < nw ? red[lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) w2 = fmax(w2, __shfl_xor_sync(0xffffffffu, w2, o));
+            if (lane == 0 && w2 > 0.0) {
+                const double err = ctl->dt * sqrt(w2);
+                atomicMax(&ctl->err_bits, (unsigned long long)__double_as_longlong(err));
+            }
+        }
+    }
+}
+
 // RKF45 step control on the device.
 __global__ void k_controller(Control* ctl, int method) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -597,6 +739,31 @@ __global__ void k_bb_update(Params<T> p, T* __restrict__ m, const T* __restrict_
 template <typename T, int METHOD, int S>
 int launch_stage(mm_ctx* ctx, const Params<T>& p, const void* m_in, const void* m0, void* m_out, T* const* kdev) {
     KernelTimer kt(ctx, MM_K_STAGE);
+    if constexpr (sizeof(T) == 8) {
+        if (ctx->fft_mode == MM_FFT_FF && !p.Ms_cell && !p.A_cell && p.Ms != 0.0 && !p.dmi && !p.stt) {
+            KPtrsD kb;
+            for (int s = 0; s < 6; ++s) kb.k[s] = (double*)ctx->k[s];
+            const double inv = 1.0 / (double)p.Ms;
+            FFStageCoef c;
+            c.wx = ff((double)(p.A * p.cx) * inv);
+            c.wy = ff((double)(p.A * p.cy) * inv);
+            c.wz = ff((double)(p.A * p.cz) * inv);
+            c.anis = ff((double)p.anis * inv);
+            c.ux = ff((double)p.ux);
+            c.uy = ff((double)p.uy);
+            c.uz = ff((double)p.uz);
+            c.hx = ff((double)p.hx);
+            c.hy = ff((double)p.hy);
+            c.hz = ff((double)p.hz);
+            c.pref = ff((double)p.pref);
+            c.alpha = ff((double)p.alpha);
+            k_stage_ff<METHOD, S><<<blocks_for(p.N), kThreads, 0, ctx->stream>>>(
+                c, p.nx, p.ny, p.nz, p.N, (const double*)m_in, (const double*)ctx->Hd, (const double*)m0, kb,
+                (double*)m_out, ctx->ctl);
+            MM_LAUNCH_CHECK(ctx);
+            return MM_OK;
+        }
+    }
     if constexpr (sizeof(T) == 4) {
         if (!p.Ms_cell && !p.A_cell && p.Ms != 0.f && p.nx % 4 == 0 && !p.dmi && !p.stt) {
             KPtrs kb;

@@ -1,9 +1,11 @@
-"""GPU parity of the float-float demag passes (MM_FFT_FF on an MM_F64
-context) against the float64 CPU oracle, at the float64 path's tolerance
+"""GPU parity of the float-float mode (MM_FFT_FF on an MM_F64 context: the
+demag passes, and for uniform material the stage kernel, in float-float
+arithmetic) against the float64 CPU oracle, at the float64 path's tolerance
 (relative L2 1e-12 per field): demag on the power-of-two meshes of the main
 parity suite, per-cell Ms with vacuum, a 128 x 128 x 16 film, RK4 steps
-checked one by one, the transpose (dot-product) test of the adjoint, and the
-mode's error paths."""
+checked one by one, an RKF45 trial (state, error estimate, proposal) and a
+rejected-then-accepted step, the transpose (dot-product) test of the
+adjoint, and the mode's error paths."""
 
 import numpy as np
 import pytest
@@ -155,4 +157,54 @@ def test_ff_mode_errors():
     with pytest.raises(mm.MMError) as e:
         mm.mm_set_fft_mode(ctx, mm.MM_FFT_FF)
     assert e.value.code == mm.MM_ERR_INVALID_ARG
+    mm.mm_destroy(ctx)
+
+
+def _rkf45_error_bound(p, m, dt, unit_roundoff):
+    """Rounding bound of the embedded error estimate dt |sum_j e_j k_j|: the
+    stage slopes carry a relative error of order the unit roundoff, so the
+    estimate is uncertain by about u * dt * max_cell sum_j |e_j| |k_j|."""
+    k = []
+    for s in range(6):
+        ms = m.copy()
+        for j in range(s):
+            ms = ms + dt * micromag.FEHLBERG_A[s][j] * k[j]
+        k.append(p.rhs(ms))
+    e = [b5 - b4 for b5, b4 in zip(micromag.FEHLBERG_B5, micromag.FEHLBERG_B4)]
+    mag = sum(abs(e[j]) * np.sqrt(np.sum(k[j] ** 2, axis=0)) for j in range(6))
+    return unit_roundoff * dt * float(np.max(mag))
+
+
+def test_ff_rkf45_trial_matches_oracle():
+    """One RKF45 trial with the float-float stage kernel (uniform material):
+    the 4th-order state at 1e-12, the error estimate within the float-float
+    rounding bound (unit roundoff 2^-48), and the controller's proposal."""
+    n, d = (16, 16, 2), (2.5e-9, 2.5e-9, 3e-9)
+    p = micromag.Problem(n, d, alpha=0.1, Ku=2e5, u=(0, 0, 1), h_ext=(2e4, 0, 0))
+    m = wl.random_unit(n, seed=4)
+    ctx = ff_ctx(p)
+    md = dev(m)
+    dt = 2e-14
+    t, dt_next, err = mm.mm_llg_step(ctx, md, 0.0, dt, mm.MM_RKF45, tol=1.0)   # accepted at any error
+    m4, err_o = p.rkf45_trial(m, dt)
+    assert t == dt
+    assert rel_l2(host(md), m4) < TOL
+    assert np.max(np.abs(np.linalg.norm(host(md), axis=0) - 1)) < 1e-14
+    assert abs(err - err_o) < 8 * _rkf45_error_bound(p, m, dt, 2.0 ** -48) + 1e-9 * err_o
+    assert dt_next == pytest.approx(micromag.next_dt(dt, err, 1.0), rel=1e-12)
+    mm.mm_destroy(ctx)
+
+
+def test_ff_rkf45_rejects_then_accepts():
+    n, d = (8, 8, 2), (2.5e-9, 2.5e-9, 3e-9)
+    p = micromag.Problem(n, d, alpha=0.02, Ku=1e5, u=(0.0, 0.6, 0.8), h_ext=(1e4, 0.0, -2e4))
+    m = wl.random_unit(n, seed=11)
+    ctx = ff_ctx(p)
+    md = dev(m)
+    t, dt_next, err = mm.mm_llg_step(ctx, md, 0.0, 1e-11, mm.MM_RKF45, tol=1e-5)
+    mo, to, dto, erro, rej = micromag.rkf45_step(p, m, 0.0, 1e-11, 1e-5)
+    assert rej >= 1
+    assert t == pytest.approx(to, rel=1e-12)
+    assert err <= 1e-5
+    assert rel_l2(host(md), mo) < TOL
     mm.mm_destroy(ctx)
