@@ -247,9 +247,12 @@ int mm_rk4_trajectory(mm_ctx* ctx, void* m, double dt, long nsteps);
 
 /* Reverse pass of mm_rk4_trajectory from m0: lam = dL/dm_N on entry,
  * dL/dm_0 on return; gMs += dL/dMs.  Checkpoints the state every
- * checkpoint_every steps (<= 0: ceil(sqrt(nsteps))) and recomputes each
+ * checkpoint_every steps (<= 0: ceil(sqrt(nsteps))) and replays each
  * segment before pulling back through it, so memory is about
- * (nsteps / K + K) states; that store is allocated for the call and freed
+ * (nsteps / K + K) states.  While a segment is replayed, each step's stage
+ * states, demag fields and slopes (10 K states) are recorded when they fit
+ * in 16 GiB, so the step VJPs need not recompute them; otherwise each step
+ * VJP recomputes its stages.  All of it is allocated for the call and freed
  * before it returns. */
 int mm_rk4_trajectory_vjp(mm_ctx* ctx, const void* m0, double dt, long nsteps, void* lam, void* gMs,
                           long checkpoint_every);

@@ -17,8 +17,9 @@
 //   anisotropy H_an = 2 Ku/(mu0 Ms) (m.u) u: d/dm = 2 Ku/(mu0 Ms) (g.u) u,
 //          d/dMs = -g . H_an / Ms.
 // The RK4 step (classic tableau, then m <- u / |u|) is reversed stage by
-// stage after recomputing the stage states from m_n; the renormalisation
-// pulls back as (lam - (lam . m_out) m_out) / |u|.
+// stage from its stage states (recorded while the checkpoint segment is
+// replayed, or recomputed from m_n); the renormalisation pulls back as
+// (lam - (lam . m_out) m_out) / |u|.
 #include <algorithm>
 #include <cmath>
 
@@ -28,6 +29,8 @@ namespace mm {
 namespace {
 
 constexpr int kT = 256;
+// largest forward tape a trajectory VJP allocates (bytes)
+constexpr size_t kTapeBudget = (size_t)16 << 30;
 inline unsigned nblk(long n) { return (unsigned)((n + kT - 1) / kT); }
 
 template <typename T> __device__ __forceinline__ V3<T> cross(V3<T> a, V3<T> b) {
@@ -222,8 +225,43 @@ int ensure_workspace(mm_ctx* ctx) {
     return MM_OK;
 }
 
+// One RK4 step's forward record, written while a checkpoint segment is
+// replayed so the step VJP need not recompute it: the stage states X1..X3,
+// the demag fields of X0..X3 and the slopes k0..k2.
+struct StepTape {
+    void* X[3];
+    void* H[4];
+    void* k[3];
+};
+
+// One RK4 step from m, recording its tape; m_next = NULL stops after the
+// demag field of X3 (the last step of a segment, whose successor is known).
+int rk4_step_record(mm_ctx* ctx, const void* m, void* m_next, const StepTape& tp) {
+    const size_t v = 3 * (size_t)ctx->N * (ctx->prec == MM_F64 ? sizeof(double) : sizeof(float));
+    void* hd_saved = ctx->Hd;
+    int rc = MM_OK;
+    const void* Xs = m;
+    for (int s = 0; s < 4 && rc == MM_OK; ++s) {
+        ctx->Hd = tp.H[s];
+        rc = demag_apply(ctx, Xs, tp.H[s]);
+        if (rc || (s == 3 && !m_next)) break;
+        void* out = s < 3 ? tp.X[s] : m_next;
+        rc = rk_stage(ctx, MM_RK4, s, Xs, m, out);
+        if (!rc && s < 3) {
+            cudaError_t ce = cudaMemcpyAsync(tp.k[s], ctx->k[s], v, cudaMemcpyDeviceToDevice, ctx->stream);
+            if (ce != cudaSuccess) rc = fail(ctx, MM_ERR_CUDA, "tape copy: %s", cudaGetErrorString(ce));
+        }
+        Xs = out;
+    }
+    ctx->Hd = hd_saved;
+    return rc;
+}
+
+// reset: put dt into the control block first (a standalone call); the
+// trajectory VJP sets it once for all its steps.  tape: the step's forward
+// record, or NULL to recompute it here.
 template <typename T>
-int step_vjp(mm_ctx* ctx, const T* m0, double dt, T* lam, T* gMs) {
+int step_vjp(mm_ctx* ctx, const T* m0, double dt, T* lam, T* gMs, const StepTape* tape = nullptr, bool reset = true) {
     int rc = ensure_workspace(ctx);
     if (rc) return rc;
     const long n3 = 3 * ctx->N;
@@ -234,23 +272,31 @@ int step_vjp(mm_ctx* ctx, const T* m0, double dt, T* lam, T* gMs) {
     T* G = w + 11 * n3;
     T* P = w + 12 * n3;
     T* D = w + 13 * n3;
-    if ((rc = ctl_reset_push(ctx, 0.0, dt, INFINITY, 1.0))) return rc;
-    // recompute the stage states X_s and their demag fields
-    void* hd_saved = ctx->Hd;
-    for (int s = 0; s < 3 && rc == MM_OK; ++s) {
-        ctx->Hd = Hst[s];
-        rc = demag_apply(ctx, X[s], Hst[s]);
-        if (!rc) rc = rk_stage(ctx, MM_RK4, s, X[s], m0, X[s + 1]);
+    const T* kk[3] = {(const T*)ctx->k[0], (const T*)ctx->k[1], (const T*)ctx->k[2]};
+    if (reset && (rc = ctl_reset_push(ctx, 0.0, dt, INFINITY, 1.0))) return rc;
+    if (tape) {
+        for (int s = 0; s < 3; ++s) {
+            X[s + 1] = (T*)tape->X[s];
+            kk[s] = (const T*)tape->k[s];
+        }
+        for (int s = 0; s < 4; ++s) Hst[s] = (T*)tape->H[s];
+    } else {
+        // recompute the stage states X_s and their demag fields
+        void* hd_saved = ctx->Hd;
+        for (int s = 0; s < 3 && rc == MM_OK; ++s) {
+            ctx->Hd = Hst[s];
+            rc = demag_apply(ctx, X[s], Hst[s]);
+            if (!rc) rc = rk_stage(ctx, MM_RK4, s, X[s], m0, X[s + 1]);
+        }
+        ctx->Hd = hd_saved;
+        if (rc) return rc;
+        if ((rc = demag_apply(ctx, X[3], Hst[3]))) return rc;
     }
-    ctx->Hd = hd_saved;
-    if (rc) return rc;
-    if ((rc = demag_apply(ctx, X[3], Hst[3]))) return rc;
     Params<T> p = make_params<T>(ctx);
     {
         KernelTimer kt(ctx, MM_K_STAGE);
-        k_vjp_norm<T><<<nblk(ctx->N), kT, 0, ctx->stream>>>(p, m0, (const T*)ctx->k[0], (const T*)ctx->k[1],
-                                                            (const T*)ctx->k[2], X[3], Hst[3], (T)dt, lam, lk[0],
-                                                            lk[1], lk[2], lk[3]);
+        k_vjp_norm<T><<<nblk(ctx->N), kT, 0, ctx->stream>>>(p, m0, kk[0], kk[1], kk[2], X[3], Hst[3], (T)dt, lam,
+                                                            lk[0], lk[1], lk[2], lk[3]);
         MM_LAUNCH_CHECK(ctx);
     }
     // classic RK4: X_1 = m0 + dt/2 k_0, X_2 = m0 + dt/2 k_1, X_3 = m0 + dt k_2
@@ -400,23 +446,51 @@ int mm_rk4_trajectory_vjp(mm_ctx* ctx, const void* m0, double dt, long nsteps, v
         const long len = std::min(K, nsteps - c * K);
         if (rc == MM_OK && c + 1 < nchk) rc = rk4_steps(ctx, seg, len);
     }
-    // reverse sweep: recompute each segment's states, then pull lam back through them
+    // the forward record of one segment (10 states per step) when it fits
+    // the tape budget; otherwise each step VJP recomputes its stages
+    char* tape = nullptr;
+    if ((size_t)10 * v * (size_t)K <= kTapeBudget && cudaMalloc((void**)&tape, (size_t)10 * v * (size_t)K) != cudaSuccess) {
+        cudaGetLastError();
+        tape = nullptr;
+    }
+    auto tape_of = [&](long j) {
+        StepTape t;
+        char* b = tape + (size_t)j * 10 * v;
+        for (int q = 0; q < 3; ++q) t.X[q] = b + q * v;
+        for (int q = 0; q < 4; ++q) t.H[q] = b + (3 + q) * v;
+        for (int q = 0; q < 3; ++q) t.k[q] = b + (7 + q) * v;
+        return t;
+    };
+    // reverse sweep: replay each segment from its checkpoint, then pull lam
+    // back through its steps (dt stays in the control block throughout)
     for (long c = nchk - 1; c >= 0 && rc == MM_OK; --c) {
         const long len = std::min(K, nsteps - c * K);
         cp(seg, chk + c * v);
-        for (long j = 1; j < len && rc == MM_OK; ++j) {
-            cp(seg + j * v, seg + (j - 1) * v);
-            if (rc == MM_OK) rc = rk4_steps(ctx, seg + j * v, 1);
+        if (tape) {
+            for (long j = 0; j < len && rc == MM_OK; ++j)
+                rc = rk4_step_record(ctx, seg + j * v, j + 1 < len ? seg + (j + 1) * v : nullptr, tape_of(j));
+        } else {
+            for (long j = 1; j < len && rc == MM_OK; ++j) {
+                cp(seg + j * v, seg + (j - 1) * v);
+                if (rc == MM_OK) rc = rk4_steps(ctx, seg + j * v, 1);
+            }
         }
         for (long j = len - 1; j >= 0 && rc == MM_OK; --j) {
+            StepTape t;
+            const StepTape* tp = nullptr;
+            if (tape) {
+                t = tape_of(j);
+                tp = &t;
+            }
             if (ctx->prec == MM_F64)
-                rc = step_vjp<double>(ctx, (const double*)(seg + j * v), dt, (double*)lam, (double*)gMs);
+                rc = step_vjp<double>(ctx, (const double*)(seg + j * v), dt, (double*)lam, (double*)gMs, tp, false);
             else
-                rc = step_vjp<float>(ctx, (const float*)(seg + j * v), dt, (float*)lam, (float*)gMs);
+                rc = step_vjp<float>(ctx, (const float*)(seg + j * v), dt, (float*)lam, (float*)gMs, tp, false);
         }
     }
     if (rc == MM_OK) rc = status_check(ctx);
     cudaStreamSynchronize(ctx->stream);
+    cudaFree(tape);
     cudaFree(chk);
     cudaFree(seg);
     return rc;
