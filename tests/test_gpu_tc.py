@@ -72,9 +72,10 @@ def test_fft_mode_rejected_for_fp64():
 
 def test_cube256_per_field_errors_and_speed():
     """256^3 bulk cube, 1 nm cells, Ku 5e5 along z, random m: relative L2 of
-    each field (demag, exchange, effective, and the torque m x H_eff) for plain FP32 and the two tensor-core modes against the
-    float64 GPU path (itself pinned to the oracle at 1e-12), and the demag
-    time per evaluation of each mode (printed)."""
+    each field (demag, exchange, effective, and the torque m x H_eff) for
+    plain FP32, the two tensor-core modes and the float-float FP64 mode
+    against the float64 GPU path (itself pinned to the oracle at 1e-12), and
+    the demag time per evaluation of each mode (printed)."""
     import workloads as wl
     n, d = (256, 256, 256), (1e-9, 1e-9, 1e-9)
     m = wl.random_unit(n, seed=11)
@@ -112,7 +113,7 @@ def test_cube256_per_field_errors_and_speed():
     ref, t64 = fields(mm.MM_F64)
     rows = {}
     for name, prec, mode in (("fp32", mm.MM_F32, 0), ("tf32x2", mm.MM_F32, mm.MM_TC_TF32),
-                             ("bf16x3", mm.MM_F32, mm.MM_TC_BF16)):
+                             ("bf16x3", mm.MM_F32, mm.MM_TC_BF16), ("ff", mm.MM_F64, mm.MM_FFT_FF)):
         out, t = fields(prec, mode)
         errs = {k: float(torch.linalg.vector_norm(out[k] - ref[k]) / torch.linalg.vector_norm(ref[k])) for k in ref}
         rows[name] = (errs, t)
@@ -121,6 +122,7 @@ def test_cube256_per_field_errors_and_speed():
     assert rows["fp32"][0]["demag"] < 1e-5 and rows["fp32"][0]["effective"] < 1e-5
     assert rows["tf32x2"][0]["demag"] < 1e-5
     assert rows["bf16x3"][0]["demag"] < 1e-4
+    assert max(rows["ff"][0].values()) < 1e-12       # float-float passes at the float64 tolerance
     del ref
     torch.cuda.empty_cache()
 
