@@ -208,3 +208,29 @@ def test_ff_rkf45_rejects_then_accepts():
     assert err <= 1e-5
     assert rel_l2(host(md), mo) < TOL
     mm.mm_destroy(ctx)
+
+
+@pytest.mark.parametrize("case", ["dmi", "per_cell_ms"])
+def test_ff_rk4_steps_with_the_fp64_stage(case):
+    """Materials outside the float-float stage kernel (interfacial DMI; per-cell
+    Ms) keep the float64 stage beside the float-float demag
+    passes: 15 RK4 steps, each against the oracle's step from the GPU's
+    previous state at 1e-12."""
+    n, d = (16, 16, 2), (2.5e-9, 2.5e-9, 2.5e-9)
+    if case == "dmi":
+        p = micromag.Problem(n, d, alpha=0.1, D=4e-3, dmi="interfacial")
+    else:
+        Ms = wl.smooth_field(n, 4e5, 9e5, sigma_cells=2.0, seed=7)
+        p = micromag.Problem(n, d, alpha=0.1, Ms_cell=Ms)
+    ctx = ff_ctx(p)
+    if case == "dmi":
+        mm.mm_set_dmi(ctx, 4e-3, mm.MM_DMI_INTERFACIAL)
+    m = wl.random_unit(n, seed=6)
+    md = dev(m)
+    prev, t = m, 0.0
+    for _ in range(15):
+        t, _, _ = mm.mm_llg_step(ctx, md, t, 5e-14, mm.MM_RK4)
+        cur = host(md)
+        assert rel_l2(cur, p.rk4_step(prev, 5e-14)) < TOL
+        prev = cur
+    mm.mm_destroy(ctx)
