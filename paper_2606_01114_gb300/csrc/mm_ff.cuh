@@ -1,4 +1,5 @@
-// Float-float ("double-single") arithmetic for the FP64 demag passes.
+// Float-float ("double-single") arithmetic for the float-float mode of FP64
+// contexts: the demag passes and, for uniform material, the LLG stage.
 //
 // GB300 runs FP64 at about 2 FMA per SM per clock, against 128 FP32 lanes.
 // A value is carried as the unevaluated sum h + l of two floats (about 48
@@ -27,8 +28,9 @@ struct ff {
     __host__ __device__ constexpr ff(float hi, float lo) : h(hi), l(lo) {}
     __host__ __device__ constexpr ff(int v) : h((float)v), l(0.f) {}
     __host__ __device__ constexpr ff(float v) : h(v), l(0.f) {}
-    // rounding split of a double constant: exact arithmetic, folded at
-    // compile time for literals (runtime data goes through d2ff)
+    // rounding split of a double (d - h is exact in double); folded at
+    // compile time for constants (runtime data goes through d2ff, which
+    // needs no FP64 arithmetic)
     __host__ __device__ constexpr ff(double d) : h((float)d), l((float)(d - (double)(float)d)) {}
 };
 
