@@ -3,7 +3,12 @@
 // computed on a grid padded to P = 2n per axis (1 when n = 1), transforms
 // unnormalised, inverse scaled once at the end.
 //
-// Five passes over HBM, each a batched shared-memory FFT (mm_fft.cuh):
+// Five passes over HBM.  In FP32, for the common lengths, the passes are
+// register-resident four-step DFTs (mm_regfft.cuh: k_xfwd_reg, k_cols_reg,
+// k_zconv_reg, k_xinv_reg); otherwise, and in FP64, each is a batched
+// shared-memory FFT (mm_fft.cuh).  An FP64 context in float-float mode runs
+// the same generic kernels on (h + l) float pairs (mm_ff.cuh, apply_ff).
+// The passes:
 //   K2 x-forward: real rows of M (only the nx non-zero values are read) are
 //      packed two-reals-per-complex into a length Px/2 complex FFT, then
 //      unpacked to the Hx = nx + 1 non-redundant frequencies;
