@@ -234,3 +234,45 @@ def test_ff_rk4_steps_with_the_fp64_stage(case):
         assert rel_l2(cur, p.rk4_step(prev, 5e-14)) < TOL
         prev = cur
     mm.mm_destroy(ctx)
+
+
+def test_ff_demag_film512_sampled_cells():
+    """The bench workload at full size (512 x 512 x 16 film, vortex with 5 %
+    noise) in float-float mode: 8 sampled cells against the oracle's direct
+    sum over all 4.2 M sources, at the float64 tolerance."""
+    w = wl.WORKLOADS["film512"]
+    p = micromag.Problem(w["n"], w["d"], Ms=w["Ms"], A=w["A"], alpha=w["alpha"])
+    m = wl.vortex(w["n"], w["d"], noise=0.05, seed=1)
+    ctx = ff_ctx(p)
+    H = torch.empty(ctx.shape3, dtype=torch.float64, device="cuda")
+    mm.mm_demag_field(ctx, dev(m), H)
+    got = host(H)
+    targets = [(0, 0, 0), (511, 511, 15), (256, 256, 8), (255, 256, 0), (0, 300, 7), (511, 17, 3),
+               (100, 400, 15), (383, 129, 9)]
+    ref = p.demag_direct(m, targets)
+    sel = np.stack([got[:, z, y, x] for (x, y, z) in targets], axis=1)
+    assert rel_l2(sel, ref) < TOL
+    mm.mm_destroy(ctx)
+
+
+def test_ff_trajectory_gradient_matches_oracle_8x8x1():
+    """The adjoint of a 40-step RK4 trajectory with the float-float demag
+    passes (forward, replay and transposed demag all in float-float) against
+    the oracle's float64 gradient of the same loss, every cell."""
+    from oracle import adjoint
+    from paper_2606_01114_gb300.autograd import RK4Trajectory
+    n, d = (8, 8, 1), (3e-9, 3e-9, 3e-9)
+    Ms = wl.smooth_field(n, 4e5, 9e5, sigma_cells=2.0, seed=3)
+    m0 = wl.random_unit(n, seed=8)
+    dt, nsteps, target = 1e-13, 40, 0.05
+    p = micromag.Problem(n, d, Ms_cell=Ms, alpha=0.02)
+    ctx = ff_ctx(p)
+    Ms_t = dev(Ms).requires_grad_(True)
+    mN = RK4Trajectory.apply(dev(m0), Ms_t, ctx, dt, nsteps, 7)
+    L = (mN[2].mean() - target) ** 2
+    L.backward()
+    g_gpu = Ms_t.grad.detach().cpu().numpy()
+    g_ref = adjoint.grad_ms(p, m0, dt, nsteps, target).reshape(n[2], n[1], n[0])
+    assert float(L.detach()) == pytest.approx(adjoint.loss(p, m0, dt, nsteps, target), rel=1e-10)
+    assert np.linalg.norm(g_gpu - g_ref) / np.linalg.norm(g_ref) < 1e-6
+    mm.mm_destroy(ctx)
