@@ -94,6 +94,33 @@ __device__ __forceinline__ void block_sum_atomic(double v, double* target) {
     }
 }
 
+// Block reductions of per-thread values of the path's type T: the warp
+// stage runs in T (FP32 adds for FP32 contexts: GB300's FP64 rate is far
+// lower), the eight warp results are combined in double by warp 0, then one
+// atomic per block.  Must be called by every thread of the block.
+template <typename T>
+__device__ __forceinline__ double block_reduce_t(T v, bool is_max) {
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        const T u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = is_max ? (u > v ? u : v) : v + u;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = (double)v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        r = lane < nw ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            const double u = __shfl_xor_sync(0xffffffffu, r, o);
+            r = is_max ? fmax(r, u) : r + u;
+        }
+    }
+    return r;   // valid in thread 0
+}
+
 // ------------------------------------------------------------- fields
 // mode 0: exchange only; mode 1: Hd + exchange + anisotropy + Zeeman
 template <typename T, int MODE>
@@ -656,7 +683,7 @@ __global__ void k_bb_grad(Params<T> p, const T* __restrict__ m, const T* __restr
                           const T* __restrict__ g_prev, const T* __restrict__ m_prev, int have_prev, Control* ctl) {
     if (ctl->status != 0 || ctl->done) return;
     long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    double tq = 0.0, ss = 0.0, sy = 0.0, yy = 0.0;
+    T tq2 = 0, ss = 0, sy = 0, yy = 0;   // squared torque and the BB sums, in the path's type
     if (i < p.N) {
         int x, y, z;
         decompose(i, p.nx, p.ny, x, y, z);
@@ -674,27 +701,32 @@ __global__ void k_bb_grad(Params<T> p, const T* __restrict__ m, const T* __restr
                              (hx.z + l.z + d.z + q.z) * inv};
             const V3<T> a = {mi.y * h.z - mi.z * h.y, mi.z * h.x - mi.x * h.z, mi.x * h.y - mi.y * h.x};   // m x h
             gi = {mi.y * a.z - mi.z * a.y, mi.z * a.x - mi.x * a.z, mi.x * a.y - mi.y * a.x};            // m x (m x h)
-            tq = sqrt((double)a.x * a.x + (double)a.y * a.y + (double)a.z * a.z);
-            if (!isfinite(tq)) tq = 1e300;
+            tq2 = a.x * a.x + a.y * a.y + a.z * a.z;
+            if (!isfinite(tq2)) tq2 = sizeof(T) == 4 ? (T)3.0e38f : (T)1e300;
         }
         if (have_prev) {
             const V3<T> mp = load3(m_prev, i, p.N), gp = load3(g_prev, i, p.N);
-            const double sx = (double)mi.x - mp.x, sy_ = (double)mi.y - mp.y, sz = (double)mi.z - mp.z;
-            const double yx = (double)gi.x - gp.x, yy_ = (double)gi.y - gp.y, yz = (double)gi.z - gp.z;
+            const T sx = mi.x - mp.x, sy_ = mi.y - mp.y, sz = mi.z - mp.z;
+            const T yx = gi.x - gp.x, yy_ = gi.y - gp.y, yz = gi.z - gp.z;
             ss = sx * sx + sy_ * sy_ + sz * sz;
             sy = sx * yx + sy_ * yy_ + sz * yz;
             yy = yx * yx + yy_ * yy_ + yz * yz;
         }
         store3(g, i, p.N, gi);
     }
-    block_max_atomic(tq, &ctl->torque_bits);
+    // the torque maximum as the maximum squared norm, one square root per block
+    const double t2 = block_reduce_t<T>(tq2, true);
+    if (threadIdx.x == 0 && t2 > 0.0) {
+        const double tq = t2 >= (sizeof(T) == 4 ? 3.0e38 : 1e300) ? 1e300 : sqrt(t2);
+        atomicMax(&ctl->torque_bits, (unsigned long long)__double_as_longlong(tq));
+    }
     if (have_prev) {
-        __syncthreads();
-        block_sum_atomic(ss, &ctl->bb[0]);
-        __syncthreads();
-        block_sum_atomic(sy, &ctl->bb[1]);
-        __syncthreads();
-        block_sum_atomic(yy, &ctl->bb[2]);
+        const double a0 = block_reduce_t<T>(ss, false);
+        if (threadIdx.x == 0) atomicAdd(&ctl->bb[0], a0);
+        const double a1 = block_reduce_t<T>(sy, false);
+        if (threadIdx.x == 0) atomicAdd(&ctl->bb[1], a1);
+        const double a2 = block_reduce_t<T>(yy, false);
+        if (threadIdx.x == 0) atomicAdd(&ctl->bb[2], a2);
     }
 }
 
