@@ -61,6 +61,10 @@ def parse():
                     help="Slonczewski current density J in A/m^2 (0: off; P 0.4, Lambda 2, p along z)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64 sub-line, the cuFFT comparison, the ALU roofs and the window statistics")
+    ap.add_argument("--relax-to", type=float, default=0.0, metavar="T",
+                    help="relax the film to simulated time T (s) in one relax() call and report that run")
     ap.add_argument("--cpu-budget", type=float, default=150.0, help="seconds of oracle work for the reference arm")
     ap.add_argument("--ingest-ncu", metavar="CSV", default=None,
                     help="write profiles/traffic.json from an ncu raw CSV export and exit")
@@ -314,12 +318,46 @@ def algorithmic_bytes(kind, n, s, Ms_cell=False):
 
 
 # ------------------------------------------------------------ CPU oracle
-def oracle_setup(w):
+class ThreadedFFT:
+    """rfftn / irfftn of scipy.fft on ``workers`` threads: the same real
+    transforms the oracle takes from numpy, spread over the host's cores
+    (used only to time the oracle; its arithmetic is unchanged)."""
+
+    def __init__(self, workers):
+        import scipy.fft
+        self._f = scipy.fft
+        self.workers = workers
+
+    def rfftn(self, a, s=None, axes=None):
+        return self._f.rfftn(a, s=s, axes=axes, workers=self.workers)
+
+    def irfftn(self, a, s=None, axes=None):
+        return self._f.irfftn(a, s=s, axes=axes, workers=self.workers)
+
+
+def host_cpu():
+    """(logical cores, CPU model) of this host."""
+    model = "unknown"
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return os.cpu_count() or 1, model
+
+
+def oracle_setup(w, workers):
     from oracle import micromag
     t0 = time.perf_counter()
     p = micromag.Problem(w["n"], w["d"], Ms=w["Ms"], A=w["A"], alpha=w["alpha"])
+    if workers > 1:
+        p.fft = ThreadedFFT(workers)
     nh = p.kernel_hat()
     p.kernel_hat = lambda: nh          # keep the transformed kernel (setup, not timed)
+    p._kernel = None
     return p, time.perf_counter() - t0
 
 
@@ -327,16 +365,32 @@ def oracle_field_eval(p, m):
     return p.demag_fft(m) + p.exchange(m)
 
 
-def cpu_baseline(w, m):
-    p, setup_s = oracle_setup(w)
+def time_oracle(p, m, evals):
     t0 = time.perf_counter()
-    oracle_field_eval(p, m)
-    dt = time.perf_counter() - t0
+    for _ in range(evals):
+        oracle_field_eval(p, m)
+    return (time.perf_counter() - t0) / evals
+
+
+def cpu_baseline(w, m):
+    """The oracle's field evaluation timed on all host cores (threaded FFT)
+    and on one thread (numpy's FFT), one evaluation each after a warm-up."""
+    cores, model = host_cpu()
     n = w["n"]
-    return {"value": 1.0 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"one demag + exchange field evaluation of the {n[0]}x{n[1]}x{n[2]} film, float64 numpy "
-                       f"(numpy FFT, one thread), {dt:.1f} s; Newell kernel setup ({setup_s:.0f} s) excluded"),
-            "llg_mcell_steps_per_s": (1.0 / dt) / 6.0 * (n[0] * n[1] * n[2]) / 1e6}
+    ncell = n[0] * n[1] * n[2]
+    p, setup_s = oracle_setup(w, cores)
+    oracle_field_eval(p, m)
+    t_all = time_oracle(p, m, 2)
+    p.fft = __import__("numpy").fft
+    t_one = time_oracle(p, m, 1)
+    return {"value": 1.0 / t_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"demag + exchange field evaluations of the {n[0]}x{n[1]}x{n[2]} film, float64 numpy with "
+                       f"scipy.fft on {cores} threads ({model}), mean of 2 after 1 warm-up: {t_all:.2f} s each; "
+                       f"Newell kernel setup ({setup_s:.0f} s) excluded"),
+            "llg_mcell_steps_per_s": (1.0 / t_all) / 6.0 * ncell / 1e6,
+            "cpu_model": model,
+            "single_thread": {"value": 1.0 / t_one, "unit": UNIT, "cores": 1,
+                              "sample": f"one evaluation with numpy's FFT on one thread: {t_one:.2f} s"}}
 
 
 def run_reference(args):
@@ -345,13 +399,11 @@ def run_reference(args):
         return 0
     w = wl.WORKLOADS[args.workload]
     n = w["n"]
+    cores, model = host_cpu()
     m = wl.vortex(n, w["d"], noise=0.05, seed=1)
-    p, setup_s = oracle_setup(w)
+    p, setup_s = oracle_setup(w, cores)
     warm = max(1, min(args.warmup, 5))          # warm-up evaluations (each takes seconds)
-    t0 = time.perf_counter()
-    for _ in range(warm):
-        oracle_field_eval(p, m)
-    t_eval = (time.perf_counter() - t0) / warm
+    t_eval = time_oracle(p, m, warm)
     steps = max(1, min(args.steps, int(args.cpu_budget // max(t_eval, 1e-3))))
     t0 = time.perf_counter()
     for _ in range(steps):
@@ -359,15 +411,15 @@ def run_reference(args):
     el = time.perf_counter() - t0
     value = steps / el
     sample = (f"{steps} demag + exchange field evaluations of the {n[0]}x{n[1]}x{n[2]} film (of {args.steps} "
-              f"requested, capped to ~{args.cpu_budget:.0f} s of oracle work), float64 numpy, one thread; "
-              f"{warm} warm-up evaluations; Newell kernel setup ({setup_s:.0f} s) excluded")
+              f"requested, capped to ~{args.cpu_budget:.0f} s of oracle work), float64 numpy with scipy.fft on "
+              f"{cores} threads ({model}); {warm} warm-up evaluations; Newell kernel setup ({setup_s:.0f} s) excluded")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": steps, "warmup": warm, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "film512: 512x512x16 cells of 2 nm, permalloy, alpha 0.5, seeded vortex + 5% noise",
                    "what": "CPU oracle field evaluation"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -375,6 +427,279 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------ GPU arm
+DEMAG = ("xfwd", "yfwd", "zconv", "yinv", "xinv")
+TIMED = DEMAG + ("stage",)
+
+# float-float cost model: FP32 instructions per operation (mm_ff.cuh: the
+# add is TwoSum + low parts + fast two-sum, the multiply TwoProd by FMA +
+# two cross FMAs + fast two-sum), and the add/multiply mix of a radix-2 FFT
+# butterfly with its complex twiddle (6 adds, 4 multiplies per 10 flops)
+FF_ADD_INSTR, FF_MUL_INSTR = 11, 7
+FF_INSTR_PER_FLOP = (6 * FF_ADD_INSTR + 4 * FF_MUL_INSTR) / 10.0
+
+
+class Run:
+    """One timed stretch of relax() (or the minimiser) on one context."""
+
+    def __init__(self, mm, ctx, m, solver):
+        self.mm, self.ctx, self.m, self.solver = mm, ctx, m, solver
+
+    def advance(self, steps):
+        mm = self.mm
+        try:
+            if self.solver == "bb":
+                mm.mm_minimize_bb(self.ctx, self.m, torque_tol=0.0, max_iter=steps)
+            else:
+                mm.mm_relax(self.ctx, self.m, t_max=5e-9, torque_tol=0.0, max_steps=steps)
+        except mm.MMError as e:          # stopping on the step cap is the expected outcome here
+            if e.code != mm.MM_ERR_NOT_CONVERGED:
+                raise
+
+    def timed(self, steps, stream, barrier=None, clocks=None):
+        import torch
+        mm = self.mm
+        mm.mm_enable_kernel_timing(self.ctx, True)
+        launches0 = mm.mm_kernel_launches(self.ctx)
+        if barrier:
+            barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        self.advance(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if barrier:
+            barrier()
+        clk = clocks.stop() if clocks else None
+        ms = ev0.elapsed_time(ev1)
+        launches = mm.mm_kernel_launches(self.ctx) - launches0
+        accepted, rejected, t_sim, _ = mm.mm_step_stats(self.ctx)
+        if self.solver == "bb":
+            accepted, rejected = steps, 0
+        kt = {name: mm.mm_kernel_time(self.ctx, k) for k, name in enumerate(mm.KERNEL_NAMES)}
+        mm.mm_enable_kernel_timing(self.ctx, False)
+        return {"ms": ms, "evals": kt["zconv"][1], "accepted": accepted, "rejected": rejected, "kt": kt,
+                "launches": launches, "clocks": clk}
+
+
+def kernel_table(kt, n, s):
+    out = {}
+    for k in TIMED:
+        t_ms, cnt = kt[k]
+        if cnt:
+            b = algorithmic_bytes(k, n, s)
+            out[k] = {"launches": cnt, "avg_us": round(1e3 * t_ms / cnt, 2), "algo_MB": round(b / 1e6, 2),
+                      "GB_s": round(b / (t_ms / 1e3 / cnt) / 1e9, 1)}
+    return out
+
+
+def path_roofline(kt, n, s, peak):
+    """Whole-path HBM view: the algorithmic bytes of every timed demag and
+    stage launch over their summed device time."""
+    byts = sum(algorithmic_bytes(k, n, s) * kt[k][1] for k in TIMED)
+    sec = sum(kt[k][0] for k in TIMED) / 1e3
+    if sec <= 0:
+        return None
+    gbs = byts / sec / 1e9
+    return {"kernels": list(TIMED), "algorithmic_GB": byts / 1e9, "kernel_s": sec, "achieved": gbs, "peak": peak,
+            "unit": "GB/s", "frac": gbs / peak}
+
+
+def hbm_roofline(dom, kt, n, s, peak, peak_src, precision):
+    tot_ms, nl = kt[dom]
+    avg_s = tot_ms / 1e3 / max(nl, 1)
+    algo = algorithmic_bytes(dom, n, s)
+    achieved = algo / avg_s / 1e9
+    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": ncu_traffic(dom, precision), "peak_source": f"{peak_src} (hbm_gbs)",
+            "algorithmic_bytes_per_launch": algo}
+
+
+def alu_roofline(dom, kt, n, peak_tflops, peak_src, hbm):
+    tot_ms, nl = kt[dom]
+    avg_s = tot_ms / 1e3 / max(nl, 1)
+    fl = algorithmic_flops(dom, n)
+    tf = fl / avg_s / 1e12
+    return {"bound": "alu", "kernel": dom, "achieved": tf, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": tf / peak_tflops, "traffic": None, "peak_source": peak_src, "algorithmic_flops_per_launch": fl,
+            "hbm": hbm}
+
+
+def measure_f64(mm, w, stream, steps, warmup, peak, peak_src, alu, e2e_steps, cufft_reps=0):
+    """The FP64 half of the metric on the same film: float-float passes and
+    stage (MM_FFT_FF, the fast FP64 path) and native FP64, each with its
+    kernel table and ALU roofline against the measured FMA roofs."""
+    import torch
+    n, d = w["n"], w["d"]
+    N = n[0] * n[1] * n[2]
+    m_host = wl.vortex(n, d, noise=0.05, seed=1)
+    out = {}
+    ctx = mm.mm_init_mesh(*n, *d, precision=mm.MM_F64, stream=stream)
+    mm.mm_set_material(ctx, w["Ms"], w["A"], w["alpha"], w["Ku"])
+    for name, mode, k_steps, k_warm in (("ff", mm.MM_FFT_FF, steps, warmup), ("native", 0, max(2, steps // 4), 2)):
+        mm.mm_set_fft_mode(ctx, mode)
+        m = torch.tensor(m_host, dtype=torch.float64, device="cuda")
+        run = Run(mm, ctx, m, "relax")
+        run.advance(k_warm)
+        r = run.timed(k_steps, stream)
+        kt = r["kt"]
+        dom = max(TIMED, key=lambda k: kt[k][0])
+        hbm = hbm_roofline(dom, kt, n, 8, peak, peak_src, "f64")
+        if name == "ff":
+            fp32 = alu["fp32_fma_tflops"]
+            roof = fp32 / 2.0 / FF_INSTR_PER_FLOP
+            src = (f"measured FP32 FMA rate {fp32:.1f} TFLOP/s (mm_alu_peak) / 2 = FP32 instructions/s, divided by "
+                   f"{FF_INSTR_PER_FLOP:.1f} FP32 instructions per FP64-equivalent flop in float-float "
+                   f"(add {FF_ADD_INSTR}, multiply {FF_MUL_INSTR}; 6 adds + 4 multiplies per butterfly)")
+        else:
+            roof = alu["fp64_fma_tflops"]
+            src = "measured FP64 FMA rate (mm_alu_peak, fma.rn.f64, 2 flops per FMA)"
+        roofline = alu_roofline(dom, kt, n, roof, src, hbm) if algorithmic_flops(dom, n) else hbm
+        entry = {"value": r["evals"] / (r["ms"] / 1e3), "unit": UNIT, "steps": k_steps, "warmup": k_warm,
+                 "ms_per_step": r["ms"] / max(r["accepted"], 1),
+                 "llg_mcell_steps_per_s": r["accepted"] * N / (r["ms"] / 1e3) / 1e6,
+                 "accepted_steps": r["accepted"], "rejected_trials": r["rejected"], "field_evals": r["evals"],
+                 "demag_ms_per_eval": sum(kt[k][0] for k in DEMAG) / max(r["evals"], 1),
+                 "roofline": roofline, "path_hbm": path_roofline(kt, n, 8, peak),
+                 "kernels": kernel_table(kt, n, 8), "gpu_launches": r["launches"],
+                 "fft": "float-float passes and stage on the FP32 pipes" if mode else "native FP64"}
+        if name == "ff" and e2e_steps > 0:
+            entry["e2e"] = e2e_host(mm, ctx, m_host, torch.float64, min(e2e_steps, 3))
+        out[name] = entry
+    if cufft_reps:
+        out["cufft"] = cufft_compare(mm, ctx, m, w["Ms"], n, cufft_reps)
+    mm.mm_destroy(ctx)
+    del m
+    return out
+
+
+def e2e_host(mm, ctx, m_host, tdtype, steps):
+    """End to end through mm_llg_step_host: each RKF45 step copies m from
+    pinned host memory to the device and back inside the call."""
+    import torch
+    import numpy as np
+    pinned = torch.from_numpy(m_host.astype(np.float64 if tdtype == torch.float64 else np.float32)).pin_memory()
+    mm.mm_enable_kernel_timing(ctx, True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    t_s, dt_s = 0.0, 1e-14
+    for _ in range(steps):
+        t_s, dt_s, _ = mm.mm_llg_step_host(ctx, pinned, t_s, dt_s, mm.MM_RKF45, 1e-5)
+    el = time.perf_counter() - t0
+    evals = mm.mm_kernel_time(ctx, mm.KERNEL_NAMES.index("zconv"))[1]
+    mm.mm_enable_kernel_timing(ctx, False)
+    nbytes = int(pinned.numel() * pinned.element_size())
+    return {"value": evals / el, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+            "steps": steps, "api": "mm_llg_step_host (RKF45): m copied host->device and device->host inside each call"}
+
+
+def cufft_compare(mm, ctx, m, Ms, n, reps):
+    """Demag through cuFFT (torch.fft R2C/C2R on the whole padded grid) with
+    the library's k-space product between the transforms: zero-padded M,
+    rfftn, -N^ M^, irfftn, crop.  Timed with CUDA events; never on the
+    library's path."""
+    import torch
+    nx, ny, nz = n
+    P = (2 * nz if nz > 1 else 1, 2 * ny if ny > 1 else 1, 2 * nx if nx > 1 else 1)
+    Mp = torch.zeros((3,) + P, dtype=m.dtype, device=m.device)
+    H = torch.empty_like(m)
+    spec = None
+
+    def once():
+        nonlocal spec
+        Mp[:, :nz, :ny, :nx] = m * Ms
+        spec = torch.fft.rfftn(Mp, dim=(1, 2, 3)).contiguous()
+        mm.mm_kspace_product(ctx, spec)
+        H.copy_(torch.fft.irfftn(spec, s=P, dim=(1, 2, 3))[:, :nz, :ny, :nx])
+
+    def ffts_only():
+        s_ = torch.fft.rfftn(Mp, dim=(1, 2, 3))
+        torch.fft.irfftn(s_, s=P, dim=(1, 2, 3))
+
+    for _ in range(3):
+        once()
+    torch.cuda.synchronize()
+    res = {}
+    for name, fn in (("per_eval", once), ("ffts_only", ffts_only)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        res[name] = a.elapsed_time(b) / reps
+    # cuFFT's compulsory traffic with unpruned transforms: read the padded M,
+    # write its spectrum, read + write it in the product (kernel octant
+    # aside), read it for the inverse, write the padded field
+    s = m.element_size()
+    padded = 3 * P[0] * P[1] * P[2] * s
+    spec_b = 3 * P[0] * P[1] * (P[2] // 2 + 1) * 2 * s
+    min_bytes = padded + spec_b + 2 * spec_b + spec_b + padded
+    out = {"demag_ms_per_eval": res["per_eval"], "ffts_only_ms": res["ffts_only"], "reps": reps,
+           "unpruned_min_GB": min_bytes / 1e9, "GB_s_on_unpruned_min": min_bytes / (res["per_eval"] / 1e3) / 1e9,
+           "what": "torch.fft rfftn/irfftn (cuFFT) on the padded grid + mm_kspace_product, pad and crop included"}
+    del Mp, spec
+    torch.cuda.empty_cache()
+    return out
+
+
+def windows(run, steps, count, stream):
+    """Field evals/s of `count` further relax() windows of `steps` steps:
+    median and 10th / 90th percentiles."""
+    import numpy as np
+    vals = []
+    for _ in range(count):
+        r = run.timed(steps, stream)
+        vals.append(r["evals"] / (r["ms"] / 1e3))
+    return {"windows": count, "steps_each": steps, "median": float(np.median(vals)),
+            "p10": float(np.percentile(vals, 10)), "p90": float(np.percentile(vals, 90)),
+            "values": [round(v, 1) for v in vals]}
+
+
+def measure_alu():
+    import paper_2606_01114_gb300 as mm
+    return {"fp64_fma_tflops": mm.mm_alu_peak(mm.MM_ROOF_FP64) / 1e12,
+            "fp32_fma_tflops": mm.mm_alu_peak(mm.MM_ROOF_FP32) / 1e12,
+            "fp32x2_fma_tflops": mm.mm_alu_peak(mm.MM_ROOF_FP32X2) / 1e12,
+            "how": "mm_alu_peak: 8 independent FMA chains per thread, 8 blocks per SM, best of 3 launches"}
+
+
+def run_relax_to(args, mm, ctx, m, n, s, stream, local):
+    """One relax() call from the vortex to t_max (adaptive RKF45, tol 1e-5,
+    first dt 1e-14 s): wall time, accepted and rejected steps, field
+    evaluations, clocks."""
+    import torch
+    N = n[0] * n[1] * n[2]
+    clocks = ClockSampler(local)
+    mm.mm_enable_kernel_timing(ctx, True)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    t_sim, steps = mm.mm_relax(ctx, m, t_max=args.relax_to, torque_tol=0.0, max_steps=10 ** 8)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    accepted, rejected, t_end, dt_last = mm.mm_step_stats(ctx)
+    kt = {name: mm.mm_kernel_time(ctx, k) for k, name in enumerate(mm.KERNEL_NAMES)}
+    mm.mm_enable_kernel_timing(ctx, False)
+    evals = kt["zconv"][1]
+    E = mm.mm_energy(ctx, m)
+    return {"metric": METRIC, "value": evals / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "dtype": args.precision + ("/ff" if args.fft_mode == "ff" else ""), "data": "synthetic",
+            "config": {"workload": f"film512 relaxation to t = {args.relax_to:g} s in one relax() call",
+                       "fft": args.fft_mode},
+            "relax": {"t_sim": t_end, "accepted_steps": accepted, "rejected_trials": rejected, "field_evals": evals,
+                      "wall_s": ms / 1e3, "mean_dt": t_end / max(accepted, 1), "last_dt": dt_last,
+                      "llg_mcell_steps_per_s": accepted * N / (ms / 1e3) / 1e6,
+                      "energies_J": [float(e) for e in E]},
+            "kernels": kernel_table(kt, n, s), "path_hbm": path_roofline(kt, n, s, load_peaks()[0]),
+            "clocks": clk}
+
+
 def run_ours(args):
     import torch
     import paper_2606_01114_gb300 as mm
@@ -412,139 +737,119 @@ def run_ours(args):
     m_host = wl.vortex(n, d, noise=0.05, seed=1)
     m = torch.tensor(m_host, dtype=tdtype, device="cuda")
 
-    def relax(steps):
-        # relax: `steps` accepted RKF45 steps; bb: `steps` minimiser iterations
-        try:
-            if args.solver == "bb":
-                mm.mm_minimize_bb(ctx, m, torque_tol=0.0, max_iter=steps)
-            else:
-                mm.mm_relax(ctx, m, t_max=5e-9, torque_tol=0.0, max_steps=steps)
-        except mm.MMError as e:          # stopping on the step cap is the expected outcome here
-            if e.code != mm.MM_ERR_NOT_CONVERGED:
-                raise
+    if args.relax_to:
+        if rank == 0:
+            print(json.dumps(run_relax_to(args, mm, ctx, m, n, s, stream, local)), flush=True)
+        mm.mm_destroy(ctx)
+        return 0
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    # warm-up
-    relax(args.warmup)
+    run = Run(mm, ctx, m, args.solver)
+    run.advance(args.warmup)
     torch.cuda.synchronize()
     # timed region: device-resident input, kernel timing on the library's stream
-    mm.mm_enable_kernel_timing(ctx, True)
-    launches0 = mm.mm_kernel_launches(ctx)
-    clocks = ClockSampler(local)
-    barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    relax(args.steps)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    launches = mm.mm_kernel_launches(ctx) - launches0
-    accepted, rejected, t_sim, dt_last = mm.mm_step_stats(ctx)
-    if args.solver == "bb":
-        accepted, rejected = args.steps, 0   # each iteration updates every cell once
-    ktimes = {name: mm.mm_kernel_time(ctx, k) for k, name in enumerate(mm.KERNEL_NAMES)}
-    mm.mm_enable_kernel_timing(ctx, False)
-    evals = ktimes["zconv"][1]           # one z-pass launch per demag evaluation
+    r = run.timed(args.steps, stream, barrier=barrier, clocks=ClockSampler(local))
+    ms, evals, accepted, rejected, kt = r["ms"], r["evals"], r["accepted"], r["rejected"], r["kt"]
     ms_max, evals_all, acc_all = reduce_over_ranks(dist, ms, evals, accepted, "cuda")
     value = evals_all / (ms_max / 1e3)
-    mcell = acc_all * N / (ms_max / 1e3) / 1e6
+    rate = acc_all * N / (ms_max / 1e3) / 1e6
 
-    # roofline of the dominant kernel (largest share of device time)
     peak, peak_src = load_peaks()
-    dom = max(("xfwd", "yfwd", "zconv", "yinv", "xinv", "stage"), key=lambda k: ktimes[k][0])
-    tot_ms, nl = ktimes[dom]
-    avg_s = tot_ms / 1e3 / max(nl, 1)
-    algo = algorithmic_bytes(dom, n, s)
-    achieved = algo / avg_s / 1e9
-    traffic = ncu_traffic(dom, args.precision)
-    kernel_share = {k: round(v[0] / max(sum(x[0] for x in ktimes.values()), 1e-9), 4) for k, v in ktimes.items()}
-    per_kernel = {}
-    for k in ("xfwd", "yfwd", "zconv", "yinv", "xinv", "stage"):
-        t_ms, cnt = ktimes[k]
-        if cnt:
-            b = algorithmic_bytes(k, n, s)
-            per_kernel[k] = {"launches": cnt, "avg_us": round(1e3 * t_ms / cnt, 2),
-                             "algo_MB": round(b / 1e6, 2), "GB_s": round(b / (t_ms / 1e3 / cnt) / 1e9, 1)}
-    demag_ms = sum(ktimes[k][0] for k in ("xfwd", "yfwd", "zconv", "yinv", "xinv"))
-    demag_bytes = sum(algorithmic_bytes(k, n, s) for k in ("xfwd", "yfwd", "zconv", "yinv", "xinv"))
-
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "peak_source": f"{peak_src} (hbm_gbs)",
-                "algorithmic_bytes_per_launch": algo}
-    fl = algorithmic_flops(dom, n)
-    if prec == mm.MM_F64 and fl and args.fft_mode != "ff":
-        # the FP64 path is bound by GB300's FP64 rate, far below its HBM roof
-        # (the float-float passes run on the FP32 pipes: HBM view)
-        tf = fl / avg_s / 1e12
-        roofline = {"bound": "alu", "kernel": dom, "achieved": tf, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
-                    "frac": tf / FP64_TFLOPS, "traffic": traffic,
-                    "peak_source": "nominal FP64 rate (152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz)",
-                    "algorithmic_flops_per_launch": fl,
-                    "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                            "algorithmic_bytes_per_launch": algo}}
+    dom = max(TIMED, key=lambda k: kt[k][0])
+    roofline = hbm_roofline(dom, kt, n, s, peak, peak_src, args.precision)
+    extras = rank == 0 and world == 1 and not args.no_extras
+    alu = measure_alu() if extras or prec == mm.MM_F64 else None
+    if prec == mm.MM_F64 and algorithmic_flops(dom, n):
+        if args.fft_mode == "ff":
+            roof = alu["fp32_fma_tflops"] / 2.0 / FF_INSTR_PER_FLOP
+            src = f"measured FP32 FMA rate / 2 / {FF_INSTR_PER_FLOP:.1f} FP32 instructions per float-float flop"
+        else:
+            roof, src = alu["fp64_fma_tflops"], "measured FP64 FMA rate (mm_alu_peak)"
+        roofline = alu_roofline(dom, kt, n, roof, src, roofline)
+    demag_ms = sum(kt[k][0] for k in DEMAG)
+    demag_bytes = sum(algorithmic_bytes(k, n, s) for k in DEMAG)
+    kernel_share = {k: round(v[0] / max(sum(x[0] for x in kt.values()), 1e-9), 4) for k, v in kt.items()}
 
     # end to end through the public API with host buffers
     e2e = None
     if args.e2e_steps > 0:
-        pinned = torch.from_numpy(m_host.astype(np.float64 if prec == mm.MM_F64 else np.float32)).pin_memory()
-        out = torch.empty_like(pinned).pin_memory()
-        mm.mm_enable_kernel_timing(ctx, True)
-        t_s, dt_s = 0.0, 1e-14
-        torch.cuda.synchronize()
-        barrier()
-        t0 = time.perf_counter()
-        trials = 0
-        for _ in range(args.e2e_steps):
-            m.copy_(pinned, non_blocking=True)
-            if args.solver == "bb":
-                relax(1)
-            else:
-                t_s, dt_s, _ = mm.mm_llg_step(ctx, m, t_s, dt_s, mm.MM_RKF45, 1e-5)
-            out.copy_(m)
-        torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        e2e_evals = mm.mm_kernel_time(ctx, mm.KERNEL_NAMES.index("zconv"))[1]   # field evaluations in the loop
-        mm.mm_enable_kernel_timing(ctx, False)
-        api = ("mm_minimize_bb (one iteration) per step" if args.solver == "bb" else "mm_llg_step (RKF45) per step")
-        e2e = {"value": e2e_evals / el * world, "unit": UNIT, "h2d_bytes_per_step": int(pinned.numel() * pinned.element_size()),
-               "d2h_bytes_per_step": int(out.numel() * out.element_size()),
-               "steps": args.e2e_steps, "api": api + ", m copied host->device before and device->host after every step"}
+        if args.solver == "bb":
+            pinned = torch.from_numpy(m_host.astype(np.float64 if prec == mm.MM_F64 else np.float32)).pin_memory()
+            mm.mm_enable_kernel_timing(ctx, True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.e2e_steps):
+                m.copy_(pinned, non_blocking=True)
+                run.advance(1)
+                pinned.copy_(m)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            ev = mm.mm_kernel_time(ctx, mm.KERNEL_NAMES.index("zconv"))[1]
+            mm.mm_enable_kernel_timing(ctx, False)
+            nb = int(pinned.numel() * pinned.element_size())
+            e2e = {"value": ev / el * world, "unit": UNIT, "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb,
+                   "steps": args.e2e_steps, "api": "mm_minimize_bb (one iteration) per step, m copied by torch"}
+        else:
+            e2e = e2e_host(mm, ctx, m_host, tdtype, args.e2e_steps)
+            e2e["value"] *= world
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, m_host)
-
+    line = None
     if rank == 0:
+        solver_note = ("Barzilai-Borwein minimiser, one field evaluation per iteration (timed steps = iterations)"
+                       if args.solver == "bb" else "relax(): adaptive RKF45")
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / max(accepted, 1), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": args.precision + ("/ff" if args.fft_mode == "ff" else ""), "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": args.precision + ("/ff" if args.fft_mode == "ff" else ""), "data": "synthetic",
             "config": {"workload": "film512: 512x512x16 cells of 2 nm (padded FFT 1024x1024x32), Ms 8e5 A/m, "
                                    "A 1.3e-11 J/m, alpha 0.5, seeded vortex + 5% noise, adaptive RKF45 tol 1e-5 "
                                    "via relax()",
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "fft": args.fft_mode,
-                       "solver": ("Barzilai-Borwein minimiser, one field evaluation per iteration (timed steps = "
-                                  "iterations)" if args.solver == "bb" else "relax(): adaptive RKF45"),
-                       "dmi_D": args.dmi, "stt_J": args.stt,
+                       "fft": args.fft_mode, "solver": solver_note, "dmi_D": args.dmi, "stt_J": args.stt,
                        "l2": "no flush: one field evaluation moves ~1.9 GB, far above the 129 MB L2"},
-            "llg_mcell_steps_per_s": mcell,
             "accepted_steps": accepted, "rejected_trials": rejected, "field_evals": evals,
             "demag_ms_per_eval": demag_ms / max(evals, 1),
             "demag_GB_s": demag_bytes / (demag_ms / 1e3 / max(evals, 1)) / 1e9,
             "roofline": roofline,
-            "kernels": per_kernel, "kernel_time_share": kernel_share,
-            "clocks": clk, "e2e": e2e, "gpu_launches": launches, "cpu_baseline": cpu,
+            "path_hbm": path_roofline(kt, n, s, peak),
+            "step_hbm_frac": (sum(algorithmic_bytes(k, n, s) * kt[k][1] for k in TIMED) / 1e9
+                              / (ms / 1e3) / peak),
+            "kernels": kernel_table(kt, n, s), "kernel_time_share": kernel_share,
+            "clocks": r["clocks"], "e2e": e2e, "gpu_launches": r["launches"],
         }
+        if args.solver == "bb":
+            line["mcell_iterations_per_s"] = acc_all * N / (ms_max / 1e3) / 1e6
+            line["llg_mcell_steps_per_s"] = None
+        else:
+            line["llg_mcell_steps_per_s"] = rate
+        if alu:
+            line["alu_peaks"] = alu
+
+    if extras:
+        line["windows"] = windows(run, 20, 5, stream)
+        if args.solver == "relax" and prec == mm.MM_F32 and args.fft_mode == "fp32" and not (args.dmi or args.stt):
+            line["cufft"] = {"f32": cufft_compare(mm, ctx, m, w["Ms"], n, 20)}
+            line["cufft"]["f32"]["ours_demag_ms_per_eval"] = line["demag_ms_per_eval"]
+            mm.mm_destroy(ctx)
+            ctx = None
+            del m
+            torch.cuda.empty_cache()
+            f64 = measure_f64(mm, w, stream, max(5, min(args.steps, 20)), 3, peak, peak_src, alu, args.e2e_steps,
+                              cufft_reps=5)
+            line["cufft"]["f64"] = f64.pop("cufft")
+            line["cufft"]["f64"]["ours_ff_demag_ms_per_eval"] = f64["ff"]["demag_ms_per_eval"]
+            line["cufft"]["f64"]["ours_native_demag_ms_per_eval"] = f64["native"]["demag_ms_per_eval"]
+            line["f64"] = f64
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, m_host)
+    if rank == 0:
         print(json.dumps(line), flush=True)
-    mm.mm_destroy(ctx)
+    if ctx is not None:
+        mm.mm_destroy(ctx)
     if dist is not None:
         dist.destroy_process_group()
     return 0

@@ -140,6 +140,15 @@ int mm_effective_field(mm_ctx* ctx, const void* m, void* H);
 int mm_llg_step(mm_ctx* ctx, void* m, double* t, double* dt, int method, double tol,
                 double* err_out);
 
+/* mm_llg_step on a host copy of the state: m_host (host [3][nz][ny][nx] of
+ * the path precision; pinned memory gives the fastest copies) is copied to a
+ * device buffer of the context, advanced by one step exactly as mm_llg_step
+ * does, and copied back before the call returns.  The first call allocates
+ * that buffer (3 N elements), kept by the context.  Errors: those of
+ * mm_llg_step, INVALID_ARG for a NULL m_host, NOMEM. */
+int mm_llg_step_host(mm_ctx* ctx, void* m_host, double* t, double* dt, int method, double tol,
+                     double* err_out);
+
 /* RKF45 relaxation (tol 1e-5, first dt 1e-14 s) until
  * max_cells |m x H_eff| / Ms <= torque_tol (checked every 10 steps) or the
  * time reaches t_max.  *t_out, *steps_out (nullable) receive the simulated
@@ -217,6 +226,33 @@ int mm_kernel_time(mm_ctx* ctx, int kernel, double* total_ms, long* launches);
  * torque): accepted steps, rejected RKF45 trials, time and next dt of the
  * last integration call.  Any pointer may be NULL. */
 int mm_step_stats(const mm_ctx* ctx, long* accepted, long* rejected, double* t, double* dt);
+
+/* Kinds of mm_alu_peak. */
+enum { MM_ROOF_FP64 = 0, MM_ROOF_FP32 = 1, MM_ROOF_FP32X2 = 2 };
+
+/* Measured arithmetic roof of this GPU for the ALU-bound paths: *flops_per_s
+ * receives the FMA throughput of a kernel that keeps 8 independent FMA
+ * chains per thread on 8 blocks per SM (best of three timed launches after
+ * one warm-up), counted as 2 flops per FMA: fma.rn.f64 (MM_ROOF_FP64, the
+ * roof of the native FP64 passes), fma.rn.f32 (MM_ROOF_FP32) or
+ * fma.rn.f32x2 on lane pairs (MM_ROOF_FP32X2; the roof of the float-float
+ * passes).  stream as in mm_init_mesh; the caller's current device is
+ * restored.  Instrumentation only: allocates and frees a small buffer and
+ * two events per call.  Errors: INVALID_ARG, CUDA. */
+int mm_alu_peak(int kind, double* flops_per_s, void* stream);
+
+/* The tensor product of the demag convolution (Eq. 4 in k-space,
+ * H^ = -N^ M^) applied in place to an UNPRUNED real-to-complex spectrum of
+ * the whole padded grid: device complex array [3][Pz][Py][Px/2+1] of the
+ * path precision (x fastest; Px, Py, Pz = 2n per axis, 1 where n = 1), the
+ * layout a library R2C transform over the three padded axes produces.  It
+ * uses the context's Newell octant with the components' parities.  An
+ * unnormalised inverse C2R transform of the result, divided by Px Py Pz and
+ * cut to the mesh, is the demagnetisation field.  This exists so that a
+ * library FFT (cuFFT) can be timed against the library's pruned passes on
+ * the same kernel; the library's own path never calls it.  Errors:
+ * INVALID_ARG, CUDA. */
+int mm_kspace_product(mm_ctx* ctx, void* spectrum);
 
 /* ---- Adjoints (gradients with respect to m and the per-cell Ms) ------------
  * The paper names automatic differentiation for inverse problems as a
@@ -367,8 +403,11 @@ int mm_relax_surrogate(mm_ctx* ctx, mm_fno* f, void* m, double t_max, double tor
  *   m, H_demag  device arrays [3][nz][ny][nx] of the given precision
  *   u_anis      anisotropy axis (NULL = z, normalised); h_ext Zeeman field in
  *               A/m (NULL = none); E_out host array of 4 doubles
- *   stream      cudaStream_t (NULL = legacy default stream); the call waits
- *               for it before returning
+ *   stream      cudaStream_t (NULL = legacy default stream of the current
+ *               device); the call waits for it before returning.  A stream
+ *               of another device is served on that device, which is made
+ *               current for the call; the caller's current device is
+ *               restored before the call returns, on success and on error
  * Scratch: block partial sums live in one fixed array of 1 MiB in the
  * library's device memory, which every GPU that loads the library keeps
  * until the process exits.  Meshes above 8,388,608 cells are rejected with

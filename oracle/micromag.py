@@ -58,6 +58,10 @@ class Problem:
             st.setdefault("d", self.n[2] * self.d[2])
             self.stt = st
         self._kernel = None
+        # the FFT namespace (rfftn / irfftn) the convolution uses: numpy's by
+        # default; a timing harness may substitute a multi-threaded one with
+        # the same functions (same transforms, different thread count)
+        self.fft = np.fft
 
     @property
     def V(self):
@@ -84,7 +88,7 @@ class Problem:
             grid = np.zeros((Pz, Py, Px))
             grid[np.ix_(np.arange(-(nz - 1), nz) % Pz, np.arange(-(ny - 1), ny) % Py,
                         np.arange(-(nx - 1), nx) % Px)] = Kr[c]
-            out.append(np.fft.rfftn(grid, axes=(0, 1, 2)))
+            out.append(self.fft.rfftn(grid, axes=(0, 1, 2)))
         return out
 
     def demag_fft(self, m):
@@ -92,13 +96,13 @@ class Problem:
         nx, ny, nz = self.n
         Px, Py, Pz = self.padded
         Nh = self.kernel_hat()
-        Mh = [np.fft.rfftn(self.Ms * m[c], s=(Pz, Py, Px), axes=(0, 1, 2)) for c in range(3)]
+        Mh = [self.fft.rfftn(self.Ms * m[c], s=(Pz, Py, Px), axes=(0, 1, 2)) for c in range(3)]
         xx, yy, zz, xy, xz, yz = Nh
         T = [[xx, xy, xz], [xy, yy, yz], [xz, yz, zz]]
         H = np.empty_like(m, dtype=np.float64)
         for i in range(3):
             Hh = -(T[i][0] * Mh[0] + T[i][1] * Mh[1] + T[i][2] * Mh[2])
-            H[i] = np.fft.irfftn(Hh, s=(Pz, Py, Px), axes=(0, 1, 2))[:nz, :ny, :nx]
+            H[i] = self.fft.irfftn(Hh, s=(Pz, Py, Px), axes=(0, 1, 2))[:nz, :ny, :nx]
         return H
 
     def demag_direct(self, m, targets=None):

@@ -29,6 +29,7 @@ MM_ERR_NOT_CONVERGED = -5
 MM_ERR_TIMEOUT = -6
 MM_ERR_NOMEM = -7
 MM_TC_TF32, MM_TC_BF16, MM_FFT_FF = 1, 2, 3
+MM_ROOF_FP64, MM_ROOF_FP32, MM_ROOF_FP32X2 = 0, 1, 2
 # kernel classes for mm_kernel_time
 MM_K_XFWD, MM_K_YFWD, MM_K_ZCONV, MM_K_YINV, MM_K_XINV, MM_K_STAGE, MM_K_CONTROL, MM_K_REDUCE = range(8)
 MM_K_COUNT = 8
@@ -103,6 +104,9 @@ def _load():
         "mm_tc_wait_selftest": (I, [L, P]),
         "mm_minimize_bb": (I, [P, P, D, L, LP]),
         "mm_relax_surrogate": (I, [P, P, P, D, D, L, I, D, D, DP, LP, LP]),
+        "mm_llg_step_host": (I, [P, P, DP, DP, I, D, DP]),
+        "mm_alu_peak": (I, [I, DP, P]),
+        "mm_kspace_product": (I, [P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -226,6 +230,27 @@ def mm_llg_step(ctx, m, t, dt, method=MM_RK4, tol=1e-5):
     tt, dd, ee = ctypes.c_double(t), ctypes.c_double(dt), ctypes.c_double(0.0)
     _check(ctx, _load().mm_llg_step(ctx.handle, _dev(ctx, m, ctx.shape3, "m"), ctypes.byref(tt), ctypes.byref(dd),
                                      int(method), float(tol), ctypes.byref(ee)))
+    return tt.value, dd.value, ee.value
+
+
+def mm_llg_step_host(ctx, m_host, t, dt, method=MM_RK4, tol=1e-5):
+    """mm_llg_step on a host array (numpy or CPU tensor, C-contiguous, shape
+    (3, nz, ny, nx), the context's dtype), updated in place.  Returns
+    (t, dt, err)."""
+    want = np.float64 if ctx.precision == MM_F64 else np.float32
+    if hasattr(m_host, "data_ptr"):
+        if getattr(m_host, "is_cuda", False) or str(m_host.dtype).split(".")[-1] != np.dtype(want).name:
+            raise ValueError(f"m_host must be a CPU {np.dtype(want).name} tensor")
+        if tuple(m_host.shape) != ctx.shape3 or not m_host.is_contiguous():
+            raise ValueError(f"m_host must be contiguous with shape {ctx.shape3}")
+        ptr = m_host.data_ptr()
+    else:
+        if m_host.dtype != want or m_host.shape != ctx.shape3 or not m_host.flags.c_contiguous:
+            raise ValueError(f"m_host must be a C-contiguous {np.dtype(want).name} array of shape {ctx.shape3}")
+        ptr = m_host.ctypes.data
+    tt, dd, ee = ctypes.c_double(t), ctypes.c_double(dt), ctypes.c_double(0.0)
+    _check(ctx, _load().mm_llg_step_host(ctx.handle, ctypes.c_void_p(ptr), ctypes.byref(tt), ctypes.byref(dd),
+                                          int(method), float(tol), ctypes.byref(ee)))
     return tt.value, dd.value, ee.value
 
 
@@ -387,6 +412,31 @@ def mm_energy_noalloc(n, d, precision, Ms, A, Ku, u, h_ext, m, H_demag, stream=N
     if rc != MM_OK:
         raise MMError(rc, lib.mm_last_error(None).decode())
     return np.array(E[:])
+
+
+def mm_alu_peak(kind=MM_ROOF_FP64, stream=None):
+    """Measured FMA throughput in flop/s (2 flops per FMA) of this GPU for
+    MM_ROOF_FP64, MM_ROOF_FP32 or MM_ROOF_FP32X2."""
+    out = ctypes.c_double(0.0)
+    lib = _load()
+    rc = lib.mm_alu_peak(int(kind), ctypes.byref(out), _stream_ptr(stream))
+    if rc != MM_OK:
+        raise MMError(rc, lib.mm_last_error(None).decode())
+    return out.value
+
+
+def mm_kspace_product(ctx, spectrum):
+    """In-place -N^ M^ on an unpruned R2C spectrum (complex tensor of shape
+    (3, Pz, Py, Px // 2 + 1) on the context's device, complex64 for MM_F32,
+    complex128 for MM_F64)."""
+    nx, ny, nz = ctx.n
+    shape = (3, 2 * nz if nz > 1 else 1, 2 * ny if ny > 1 else 1, nx + 1 if nx > 1 else 1)
+    want = "complex128" if ctx.precision == MM_F64 else "complex64"
+    if not getattr(spectrum, "is_cuda", False) or str(spectrum.dtype).split(".")[-1] != want:
+        raise ValueError(f"spectrum must be a {want} CUDA tensor")
+    if tuple(spectrum.shape) != shape or not spectrum.is_contiguous():
+        raise ValueError(f"spectrum must be contiguous with shape {shape}")
+    _check(ctx, _load().mm_kspace_product(ctx.handle, ctypes.c_void_p(spectrum.data_ptr())))
 
 
 class FNO:

@@ -90,7 +90,7 @@ size_t elem(const mm_ctx* ctx) { return ctx->prec == MM_F64 ? sizeof(double) : s
 void free_all(mm_ctx* ctx) {
     void* ptrs[] = {ctx->Ms_cell, ctx->A_cell, ctx->kern, ctx->bufA, ctx->bufB, ctx->Hd, ctx->Hs_field,
                     ctx->m0, ctx->ms[0], ctx->ms[1], ctx->mnext, ctx->kptrs, ctx->ctl, ctx->tw.f64, ctx->tw.f32,
-                    ctx->tw.ff, ctx->kern_ff, ctx->adj};
+                    ctx->tw.ff, ctx->kern_ff, ctx->adj, ctx->m_stage};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (void* p : ctx->k)
@@ -410,6 +410,27 @@ int mm_llg_step(mm_ctx* ctx, void* m, double* t, double* dt, int method, double 
         }
     }
     return fail(ctx, MM_ERR_DT_UNDERFLOW, "RKF45 rejected 200 trials in a row");
+}
+
+int mm_llg_step_host(mm_ctx* ctx, void* m_host, double* t, double* dt, int method, double tol, double* err_out) {
+    if (!ctx) return fail(nullptr, MM_ERR_INVALID_ARG, "ctx is NULL");
+    MM_BIND(ctx);
+    if (!m_host) return fail(ctx, MM_ERR_INVALID_ARG, "m_host must not be NULL");
+    const size_t bytes = 3 * (size_t)ctx->N * elem(ctx);
+    int rc;
+    if (!ctx->m_stage && (rc = alloc(ctx, &ctx->m_stage, bytes))) return rc;
+    MM_CUDA_CHECK(ctx, cudaMemcpyAsync(ctx->m_stage, m_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    if ((rc = mm_llg_step(ctx, ctx->m_stage, t, dt, method, tol, err_out))) return rc;
+    MM_CUDA_CHECK(ctx, cudaMemcpyAsync(m_host, ctx->m_stage, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    MM_CUDA_CHECK(ctx, cudaStreamSynchronize(ctx->stream));
+    return MM_OK;
+}
+
+int mm_kspace_product(mm_ctx* ctx, void* spectrum) {
+    if (!ctx) return fail(nullptr, MM_ERR_INVALID_ARG, "ctx is NULL");
+    MM_BIND(ctx);
+    if (!spectrum) return fail(ctx, MM_ERR_INVALID_ARG, "spectrum must be a device pointer");
+    return demag_kspace_product(ctx, spectrum);
 }
 
 int mm_relax(mm_ctx* ctx, void* m, double t_max, double torque_tol, long max_steps, double* t_out, long* steps_out) {

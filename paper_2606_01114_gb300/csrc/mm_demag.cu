@@ -498,75 +498,22 @@ __global__ void __launch_bounds__(3 * kZB)
     }
 }
 
-// K2 / K6 for the packed complex length L = L1 x L2 (64 <= L <= 512, L1 >=
-// L2): four-step transform of B rows through shared memory, with the
-// real-to-complex unpacking (forward) or packing (inverse) as a further
-// shared-memory pass.  Level-1 threads (t < L2) hold z[t + L2 n1]; level-2
-// threads (k1 < L1) hold row k1 of the L1 x L2 transpose, XOR-swizzled.
+// K6 for the packed complex length L = L1 x L2 (64 <= L <= 512, L1 >= L2):
+// four-step transform of B rows through shared memory, with the
+// complex-to-real packing as a further shared-memory pass before it (a
+// variant that formed the packed values in the level-1 loads instead, with
+// compile-time twiddles and no first round trip, ran 2 % slower).
+// Level-1 threads (t < L2) hold z[t + L2 n1]; level-2 threads (k1 < L1)
+// hold row k1 of the L1 x L2 transpose, XOR-swizzled (xsw, shared with K2).
 template <int L1, int L2> __device__ __forceinline__ int xsw(int k1, int n2) {
     return k1 * L2 + (n2 ^ (k1 & (L2 - 1) & 15));
 }
 
-template <int L1, int L2>
-__global__ void __launch_bounds__(128, 7)
-    k_xfwd_reg(const float* __restrict__ in, const float* __restrict__ Ms, float ms, long ms_rows,
-               float2* __restrict__ out, int Hs, long rows, const float2* __restrict__ twL,
-               const float2* __restrict__ twP) {
-    constexpr int L = L1 * L2, B = 4, NX = L;   // nx real inputs per row, L packed pairs
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* S = reinterpret_cast<float2*>(smem_raw);      // [B][L]
-    const int tid = threadIdx.x;
-    const long r0 = (long)blockIdx.x * B;
-    if (tid < B * L2) {
-        const int t = tid % L2, b = tid / L2;
-        const long r = r0 + b;
-        const bool act = r < rows;
-        const float2* rowp = reinterpret_cast<const float2*>(in + (act ? r : 0) * NX);
-        const float2* msp = Ms ? reinterpret_cast<const float2*>(Ms + ((act ? r : 0) % ms_rows) * NX) : nullptr;
-        float2 v[L1];
-#pragma unroll
-        for (int n1 = 0; n1 < L1 / 2; ++n1) {
-            const int j = t + L2 * n1;
-            float2 a = act ? rowp[j] : make_float2(0.f, 0.f);
-            if (msp) {
-                float2 w = msp[j];
-                a.x *= w.x;
-                a.y *= w.y;
-            } else {
-                a.x *= ms;
-                a.y *= ms;
-            }
-            v[n1] = a;
-        }
-        dif<L1, -1, true>(v);
-#pragma unroll
-        for (int k1 = 0; k1 < L1; ++k1) {
-            float2 y = v[dif_pos<L1>(k1)];
-            if (k1 > 0) y = cmul(y, twL[t * k1]);
-            S[b * L + xsw<L1, L2>(k1, t)] = y;
-        }
-    }
-    __syncthreads();
-    const int k1 = tid % L1, b2 = tid / L1;
-    float2 u[L2];
-#pragma unroll
-    for (int n2 = 0; n2 < L2; ++n2) u[n2] = S[b2 * L + xsw<L1, L2>(k1, n2)];
-    dif<L2, -1, false>(u);
-    __syncthreads();
-#pragma unroll
-    for (int k2 = 0; k2 < L2; ++k2) S[b2 * L + k1 + L1 * k2] = u[dif_pos<L2>(k2)];
-    __syncthreads();
-    // X_k = E_k - i w^k D_k, E, D the even/odd split of the packed spectrum Z
-    for (int idx = tid; idx < B * (L + 1); idx += blockDim.x) {
-        const int b = idx / (L + 1), k = idx - b * (L + 1);
-        const long r = r0 + b;
-        if (r >= rows) continue;
-        const float2 zk = S[b * L + (k & (L - 1))];
-        const float2 zc = cconj(S[b * L + ((L - k) & (L - 1))]);
-        const float2 e = cscale(cadd(zk, zc), 0.5f);
-        const float2 d = cscale(csub(zk, zc), 0.5f);
-        const float2 wd = cmul(twP[k], d);
-        out[r * Hs + k] = make_float2(e.x + wd.y, e.y - wd.x);
+// f(std::integral_constant<int, I>) for I = I0 .. N-1, unrolled at compile time
+template <int I, int N, typename F> __device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (I < N) {
+        f(std::integral_constant<int, I>{});
+        static_for<I + 1, N>(f);
     }
 }
 
@@ -635,6 +582,89 @@ __global__ void __launch_bounds__(128, (L1 * L2 >= 512) ? 6 : 8)
             op[k1 + L1 * k2] = make_float2(z.x * scale, z.y * scale);
         }
     }
+}
+
+// K2 for the packed complex length L = L1 x L2 (64 <= L <= 512, L1 >= L2):
+// four-step transform of B rows, level 1 through shared memory, with the
+// real-to-complex unpacking done in registers: after level 2,
+// thread (k1, b) holds Z[k1 + L1 k2] of its row, and the partner value
+// conj Z[L - k] comes from lane L1 - k1 of the same row by a warp shuffle
+// (lane 0 of the row pairs with itself, k2 <-> L2 - k2).  The twiddle w^k,
+// w = exp(-2 pi i / Px), splits into a per-thread w^k1 (one table read) and
+// a compile-time w^(L1 k2).  Each output row is written straight from
+// registers: no shared-memory round trip and no barrier after level 2.
+template <int L1, int L2>
+__global__ void __launch_bounds__(128, 7)
+    k_xfwd_reg(const float* __restrict__ in, const float* __restrict__ Ms, float ms, long ms_rows,
+                float2* __restrict__ out, int Hs, long rows, const float2* __restrict__ twL,
+                const float2* __restrict__ twP) {
+    constexpr int L = L1 * L2, B = 4, NX = L;
+    static_assert(32 % L1 == 0 || L1 % 32 == 0, "rows must not straddle warps unevenly");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* S = reinterpret_cast<float2*>(smem_raw);      // [B][L]
+    const int tid = threadIdx.x;
+    const long r0 = (long)blockIdx.x * B;
+    if (tid < B * L2) {
+        const int t = tid % L2, b = tid / L2;
+        const long r = r0 + b;
+        const bool act = r < rows;
+        const float2* rowp = reinterpret_cast<const float2*>(in + (act ? r : 0) * NX);
+        const float2* msp = Ms ? reinterpret_cast<const float2*>(Ms + ((act ? r : 0) % ms_rows) * NX) : nullptr;
+        float2 v[L1];
+#pragma unroll
+        for (int n1 = 0; n1 < L1 / 2; ++n1) {
+            const int j = t + L2 * n1;
+            float2 a = act ? rowp[j] : make_float2(0.f, 0.f);
+            if (msp) {
+                float2 w = msp[j];
+                a.x *= w.x;
+                a.y *= w.y;
+            } else {
+                a.x *= ms;
+                a.y *= ms;
+            }
+            v[n1] = a;
+        }
+        dif<L1, -1, true>(v);
+#pragma unroll
+        for (int k1 = 0; k1 < L1; ++k1) {
+            float2 y = v[dif_pos<L1>(k1)];
+            if (k1 > 0) y = cmul(y, twL[t * k1]);
+            S[b * L + xsw<L1, L2>(k1, t)] = y;
+        }
+    }
+    __syncthreads();
+    const int k1 = tid % L1, b2 = tid / L1;
+    float2 u[L2];
+#pragma unroll
+    for (int n2 = 0; n2 < L2; ++n2) u[n2] = S[b2 * L + xsw<L1, L2>(k1, n2)];
+    dif<L2, -1, false>(u);
+    const int lane = tid & 31;
+    const int partner = lane - k1 + ((L1 - k1) & (L1 - 1));
+    const long r = r0 + b2;
+    const float2 wk1 = twP[k1];
+    float2* orow = out + (r < rows ? r : 0) * Hs;
+    static_for<0, L2>([&](auto K2) {
+        constexpr int k2 = decltype(K2)::value;
+        const float2 zk = u[dif_pos<L2>(k2)];
+        const float2 zs = u[dif_pos<L2>(L2 - 1 - k2)];
+        float2 zp;
+        zp.x = __shfl_sync(0xffffffffu, zs.x, partner);
+        zp.y = __shfl_sync(0xffffffffu, zs.y, partner);
+        if (k1 == 0) zp = u[dif_pos<L2>((L2 - k2) & (L2 - 1))];
+        const float2 zc = cconj(zp);
+        const float2 e = cscale(cadd(zk, zc), 0.5f);
+        float2 d = cscale(csub(zk, zc), 0.5f);
+        if constexpr (k2 > 0) {
+            constexpr double c = cos2pi(k2, 2 * L2), sn = -sin2pi(k2, 2 * L2);
+            d = cmul(d, make_float2((float)c, (float)sn));
+        }
+        const float2 wd = cmul(wk1, d);
+        if (r < rows) orow[k1 + L1 * k2] = make_float2(e.x + wd.y, e.y - wd.x);
+        if constexpr (k2 == 0) {
+            if (k1 == 0 && r < rows) orow[L] = make_float2(zk.x - zk.y, 0.f);
+        }
+    });
 }
 
 // K3 / K5 for L = L1 x L2 (64 <= L <= 1024): four-step transform of B
@@ -1164,6 +1194,41 @@ int apply_ff(mm_ctx* ctx, const double* m, double* H, bool unit) {
     return MM_OK;
 }
 
+// The tensor product of K4 on an unpruned real-to-complex spectrum of the
+// whole padded grid, [3][Pz][Py][Hx] complex (x fastest, Hx = Px/2 + 1, the
+// layout of a library R2C transform over the three padded axes): one thread
+// per k point forms H = -N M from the stored octant with the components'
+// parities (xy odd in ky, xz odd in kz, yz odd in both).  In place.
+template <typename T>
+__global__ void k_kspace_product(C_t<T>* __restrict__ spec, const T* __restrict__ kern, int Pz, int Py, int Hx,
+                                 int Hs, int Py2, int Pz2) {
+    using C = C_t<T>;
+    const long plane = (long)Pz * Py * Hx;
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= plane) return;
+    const int kx = (int)(i % Hx);
+    const long r = i / Hx;
+    const int ky = (int)(r % Py), kz = (int)(r / Py);
+    const bool yodd = 2 * ky > Py, zodd = 2 * kz > Pz;
+    const int kyp = yodd ? Py - ky : ky, kzp = zodd ? Pz - kz : kz;
+    const long kc = (long)Pz2 * Py2 * Hs;
+    const long o = ((long)kzp * Py2 + kyp) * Hs + kx;
+    const T xx = kern[o], yy = kern[kc + o], zz = kern[2 * kc + o];
+    T xy = kern[3 * kc + o], xz = kern[4 * kc + o], yz = kern[5 * kc + o];
+    if (yodd) {
+        xy = -xy;
+        yz = -yz;
+    }
+    if (zodd) {
+        xz = -xz;
+        yz = -yz;
+    }
+    const C mx = spec[i], my = spec[plane + i], mz = spec[2 * plane + i];
+    spec[i] = cmk<C>(-(xx * mx.x + xy * my.x + xz * mz.x), -(xx * mx.y + xy * my.y + xz * mz.y));
+    spec[plane + i] = cmk<C>(-(xy * mx.x + yy * my.x + yz * mz.x), -(xy * mx.y + yy * my.y + yz * mz.y));
+    spec[2 * plane + i] = cmk<C>(-(xz * mx.x + yz * my.x + zz * mz.x), -(xz * mx.y + yz * my.y + zz * mz.y));
+}
+
 // float-float copy of an array of doubles (rounding split, once per mode switch)
 __global__ void k_split_ff(const double* __restrict__ in, ff* __restrict__ out, long n) {
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1188,6 +1253,19 @@ int demag_prepare_ff(mm_ctx* ctx) {
     k_split_ff<<<(unsigned)((nt + 255) / 256), 256, 0, ctx->stream>>>((const double*)ctx->tw.f64, (ff*)ctx->tw.ff, nt);
     MM_LAUNCH_CHECK(ctx);
     MM_CUDA_CHECK(ctx, cudaStreamSynchronize(ctx->stream));
+    return MM_OK;
+}
+
+int demag_kspace_product(mm_ctx* ctx, void* spec) {
+    const long n = (long)ctx->Pz * ctx->Py * ctx->Hx;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    if (ctx->prec == MM_F64)
+        k_kspace_product<double><<<blocks, 256, 0, ctx->stream>>>((double2*)spec, (const double*)ctx->kern, ctx->Pz,
+                                                                  ctx->Py, ctx->Hx, ctx->Hs, ctx->Py2, ctx->Pz2);
+    else
+        k_kspace_product<float><<<blocks, 256, 0, ctx->stream>>>((float2*)spec, (const float*)ctx->kern, ctx->Pz,
+                                                                 ctx->Py, ctx->Hx, ctx->Hs, ctx->Py2, ctx->Pz2);
+    MM_LAUNCH_CHECK(ctx);
     return MM_OK;
 }
 

@@ -107,6 +107,7 @@ struct mm_ctx {
     void* k[6];               // [3][N] RK stage slopes
     void* kptrs;              // device copy of k[0..5]
     void* adj;                // adjoint workspace (14 fields of [3][N]), allocated on first use
+    void* m_stage;            // [3][N] device copy of a host state (mm_llg_step_host), allocated on first use
     mm::Control* ctl;         // device control block
     mm::Control* ctl_host;    // pinned host mirror
     double* newell_host;      // [6][nz][ny][nx] real-space tensor (host copy)
@@ -185,6 +186,8 @@ int demag_setup(mm_ctx* ctx);                          // K1: Newell tensor -> k
 int demag_apply(mm_ctx* ctx, const void* m, void* H);  // K2..K6
 int demag_apply_unit(mm_ctx* ctx, const void* g, void* H);  // same with Ms = 1 (adjoint)
 int demag_prepare_ff(mm_ctx* ctx);                     // float-float tables for MM_FFT_FF
+// the tensor product of K4 on an unpruned R2C spectrum [3][Pz][Py][Hx] (in place)
+int demag_kspace_product(mm_ctx* ctx, void* spec);
 // surrogate network: its grid, and the stream its launches go to (returns the old one)
 void fno_grid(const mm_fno* f, int* nx, int* ny);
 cudaStream_t fno_swap_stream(mm_fno* f, cudaStream_t s);

@@ -165,14 +165,27 @@ extern "C" int mm_energy_noalloc(int nx, int ny, int nz, double dx, double dy, d
     if (h_ext)
         for (int c = 0; c < 3; ++c) h[c] = h_ext[c];
     cudaStream_t st = (cudaStream_t)stream;
-    int dev = 0;
-    cudaError_t e = st ? cudaStreamGetDevice(st, &dev) : cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaSetDevice(dev);
+    int caller_dev = 0, dev = 0;
+    cudaError_t e = cudaGetDevice(&caller_dev);
+    if (e == cudaSuccess) {
+        dev = caller_dev;
+        if (st) e = cudaStreamGetDevice(st, &dev);
+    }
+    if (e == cudaSuccess && dev != caller_dev) e = cudaSetDevice(dev);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(nullptr, MM_ERR_CUDA, "mm_energy_noalloc: cannot select the stream's device: %s",
                     cudaGetErrorString(e));
     }
+    // the stream's device is current for the call; the caller's current
+    // device is put back on every return path
+    struct RestoreDevice {
+        int dev;
+        bool on;
+        ~RestoreDevice() {
+            if (on) cudaSetDevice(dev);
+        }
+    } restore{caller_dev, dev != caller_dev};
     double* scratch = nullptr;
     int rc = scratch_address(dev, &scratch);
     if (rc) return rc;

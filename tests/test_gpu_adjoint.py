@@ -58,7 +58,7 @@ def test_demag_transpose_dot_product():
     gm = torch.empty_like(v)
     gMs = torch.zeros(ctx.shape1, dtype=torch.float64, device="cuda")
     mm.mm_demag_vjp(ctx, g, v, gm, gMs)
-    assert vdot(g, Hv) == pytest.approx(vdot(gm, v), rel=1e-12)
+    assert vdot(g, Hv) == pytest.approx(vdot(gm, v), rel=1e-12, abs=0)
     # H_d is linear in Ms: the Ms pull-back is exact against a central difference
     delta = dev(rng.standard_normal(ctx.shape1) * 1e4)
     Ms_t = dev(Ms)
@@ -69,7 +69,7 @@ def test_demag_transpose_dot_product():
         mm.mm_demag_field(ctx, v, H)
         return vdot(g, H)
     fd = (f(1.0) - f(-1.0)) / 2.0
-    assert fd == pytest.approx(vdot(gMs, delta), rel=1e-10)
+    assert fd == pytest.approx(vdot(gMs, delta), rel=1e-10, abs=0)
     mm.mm_destroy(ctx)
 
 
@@ -84,7 +84,7 @@ def test_exchange_transpose_dot_product_and_ms_gradient():
     gm = torch.empty_like(v)
     gMs = torch.zeros(ctx.shape1, dtype=torch.float64, device="cuda")
     mm.mm_exchange_vjp(ctx, g, v, gm, gMs)
-    assert vdot(g, Hv) == pytest.approx(vdot(gm, v), rel=1e-12)
+    assert vdot(g, Hv) == pytest.approx(vdot(gm, v), rel=1e-12, abs=0)
     delta = dev(rng.standard_normal(ctx.shape1))
     Ms_t = dev(Ms)
 
@@ -94,7 +94,7 @@ def test_exchange_transpose_dot_product_and_ms_gradient():
         mm.mm_exchange_field(ctx, v, H)
         return vdot(g, H)
     fd = richardson(f, 1e-3)
-    assert fd == pytest.approx(vdot(gMs, delta * Ms_t), rel=1e-8)
+    assert fd == pytest.approx(vdot(gMs, delta * Ms_t), rel=1e-8, abs=0)
     mm.mm_destroy(ctx)
 
 
@@ -119,9 +119,9 @@ def test_rk4_step_vjp_against_central_differences():
         return x
 
     fm = richardson(lambda e: vdot(lam0, step(m0 + e * v, Ms_t)), 1e-4)
-    assert fm == pytest.approx(vdot(lam, v), rel=1e-7)
+    assert fm == pytest.approx(vdot(lam, v), rel=1e-7, abs=0)
     fs = richardson(lambda e: vdot(lam0, step(m0, Ms_t * (1 + e * delta))), 1e-4)
-    assert fs == pytest.approx(vdot(gMs, delta * Ms_t), rel=1e-7)
+    assert fs == pytest.approx(vdot(gMs, delta * Ms_t), rel=1e-7, abs=0)
     mm.mm_destroy(ctx)
 
 
@@ -145,7 +145,7 @@ def test_trajectory_gradient_matches_oracle_8x8x1():
     g_gpu = Ms_t.grad.detach().cpu().numpy()
     p = micromag.Problem(n, d, Ms_cell=Ms, alpha=0.02)
     g_ref = adjoint.grad_ms(p, m0, dt, nsteps, target).reshape(n[2], n[1], n[0])
-    assert float(L.detach()) == pytest.approx(adjoint.loss(p, m0, dt, nsteps, target), rel=1e-10)
+    assert float(L.detach()) == pytest.approx(adjoint.loss(p, m0, dt, nsteps, target), rel=1e-10, abs=0)
     assert np.linalg.norm(g_gpu - g_ref) / np.linalg.norm(g_ref) < 1e-6
     mm.mm_destroy(ctx)
 
@@ -241,7 +241,7 @@ def test_llg_step_autograd_against_central_differences():
     def f(e):
         with torch.no_grad():
             return float(torch.sum(w * LLGStep.apply(m0.detach() + e * v, Ms_t.detach(), ctx, 5e-14)))
-    assert richardson(f, 1e-4) == pytest.approx(vdot(m0.grad, v), rel=1e-7)
+    assert richardson(f, 1e-4) == pytest.approx(vdot(m0.grad, v), rel=1e-7, abs=0)
     mm.mm_destroy(ctx)
 
 
@@ -270,4 +270,36 @@ def test_design256_gradient_time_2000_steps(design256):
     g = Ms_t.grad
     assert torch.isfinite(g).all() and float(g.abs().max()) > 0
     print(f"design256 float32, 2000 RK4 steps: forward {t1 - t0:.2f} s, gradient (forward + adjoint) {t2 - t0:.2f} s")
+    mm.mm_destroy(ctx)
+
+
+def test_design256_gradient_time_20000_steps_2ns(design256):
+    """The differentiation workload at its read horizon: 20,000 RK4 steps of
+    0.1 ps (2 ns) forward and the adjoint with sqrt(T) = 142-step
+    checkpoints, float32 (memory: 141 checkpoints plus one segment's tape).
+    The gradient is finite and non-zero; forward and total times are
+    printed."""
+    import time
+    from paper_2606_01114_gb300.autograd import RK4Trajectory
+    w, Ms, m0 = design256
+    ctx = make_ctx(w["n"], w["d"], Ms, prec=mm.MM_F32)
+    m0d = dev(m0, mm.MM_F32)
+    warm = dev(Ms, mm.MM_F32).requires_grad_(True)
+    _loss(RK4Trajectory.apply(m0d, warm, ctx, 1e-13, 2, 0), 0.05).backward()
+    Ms_t = dev(Ms, mm.MM_F32).requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mN = RK4Trajectory.apply(m0d, Ms_t, ctx, 1e-13, 20000, 0)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    L = _loss(mN, 0.05)
+    L.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    g = Ms_t.grad
+    assert torch.isfinite(g).all() and float(g.abs().max()) > 0
+    mz = float(mN[2].mean())
+    print(f"design256 float32, 20000 RK4 steps (2 ns): <m_z>(T) = {mz:.6f}, loss {float(L):.3e}, "
+          f"forward {t1 - t0:.2f} s, gradient (forward + adjoint) {t2 - t0:.2f} s, "
+          f"|dL/dMs| max {float(g.abs().max()):.3e}")
     mm.mm_destroy(ctx)

@@ -58,3 +58,48 @@ def test_noalloc_rejects_meshes_beyond_its_scratch():
                                ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(m.data_ptr()), E, None)
     assert rc == mm.MM_ERR_INVALID_ARG
     assert "exceed" in lib.mm_last_error(None).decode()
+
+
+@pytest.mark.parametrize("prec", [mm.MM_F64, mm.MM_F32], ids=["f64", "f32"])
+def test_noalloc_energy_matches_oracle(prec):
+    """The four energies against the float64 oracle's (demag energy from the
+    oracle's own convolution), within the path's tolerance of their scale."""
+    from oracle import micromag
+    from paper_2606_01114_gb300 import build
+    build.build()
+    n, d = (32, 16, 4), (2.5e-9, 2.5e-9, 3e-9)
+    Ms, A, Ku, u, h = 8e5, 1.3e-11, 2e5, (0.2, -0.3, 0.9), (1e4, -2e4, 5e3)
+    p = micromag.Problem(n, d, Ms=Ms, A=A, Ku=Ku, u=u, h_ext=h)
+    m_np = wl.random_unit(n, seed=6)
+    dtype = torch.float64 if prec == mm.MM_F64 else torch.float32
+    ctx = mm.mm_init_mesh(*n, *d, precision=prec)
+    mm.mm_set_material(ctx, Ms, A, 0.02, Ku, u)
+    m = torch.tensor(m_np, dtype=dtype, device="cuda")
+    H = torch.empty_like(m)
+    mm.mm_demag_field(ctx, m, H)
+    got = mm.mm_energy_noalloc(n, d, prec, Ms, A, Ku, u, h, m, H)
+    ref = p.energies(m_np)[:4]
+    assert np.max(np.abs(got - ref)) / np.sum(np.abs(ref)) < TOL[prec]
+    mm.mm_destroy(ctx)
+
+
+def test_noalloc_restores_the_callers_device():
+    """A stream on another device is served there; the caller's current
+    device is the same after the call as before it."""
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs two GPUs")
+    import ctypes
+    from paper_2606_01114_gb300 import build
+    build.build()
+    lib = mm._load()
+    n, d = (16, 8, 2), (2e-9, 2e-9, 2e-9)
+    with torch.cuda.device(1):
+        s1 = torch.cuda.Stream()
+        m = torch.tensor(wl.random_unit(n, seed=2), dtype=torch.float64, device="cuda:1")
+        H = torch.zeros_like(m)
+    torch.cuda.set_device(0)
+    E = (ctypes.c_double * 4)()
+    rc = lib.mm_energy_noalloc(*n, *d, mm.MM_F64, 8e5, 1.3e-11, 0.0, None, None, ctypes.c_void_p(m.data_ptr()),
+                               ctypes.c_void_p(H.data_ptr()), E, ctypes.c_void_p(s1.cuda_stream))
+    assert rc == mm.MM_OK
+    assert torch.cuda.current_device() == 0
