@@ -124,7 +124,7 @@ def test_ff_demag_transpose_dot_product():
     gMs = torch.zeros(ctx.shape1, dtype=torch.float64, device="cuda")
     mm.mm_demag_vjp(ctx, g, v, gm, gMs)
     a, b = float(torch.sum(g * Hv)), float(torch.sum(gm * v))
-    assert a == pytest.approx(b, rel=1e-12)
+    assert a == pytest.approx(b, rel=1e-12, abs=0)
     mm.mm_destroy(ctx)
 
 
@@ -191,7 +191,7 @@ def test_ff_rkf45_trial_matches_oracle():
     assert rel_l2(host(md), m4) < TOL
     assert np.max(np.abs(np.linalg.norm(host(md), axis=0) - 1)) < 1e-14
     assert abs(err - err_o) < 8 * _rkf45_error_bound(p, m, dt, 2.0 ** -48) + 1e-9 * err_o
-    assert dt_next == pytest.approx(micromag.next_dt(dt, err, 1.0), rel=1e-12)
+    assert dt_next == pytest.approx(micromag.next_dt(dt, err, 1.0), rel=1e-12, abs=0)
     mm.mm_destroy(ctx)
 
 
@@ -204,7 +204,7 @@ def test_ff_rkf45_rejects_then_accepts():
     t, dt_next, err = mm.mm_llg_step(ctx, md, 0.0, 1e-11, mm.MM_RKF45, tol=1e-5)
     mo, to, dto, erro, rej = micromag.rkf45_step(p, m, 0.0, 1e-11, 1e-5)
     assert rej >= 1
-    assert t == pytest.approx(to, rel=1e-12)
+    assert t == pytest.approx(to, rel=1e-12, abs=0)
     assert err <= 1e-5
     assert rel_l2(host(md), mo) < TOL
     mm.mm_destroy(ctx)
@@ -273,6 +273,6 @@ def test_ff_trajectory_gradient_matches_oracle_8x8x1():
     L.backward()
     g_gpu = Ms_t.grad.detach().cpu().numpy()
     g_ref = adjoint.grad_ms(p, m0, dt, nsteps, target).reshape(n[2], n[1], n[0])
-    assert float(L.detach()) == pytest.approx(adjoint.loss(p, m0, dt, nsteps, target), rel=1e-10)
+    assert float(L.detach()) == pytest.approx(adjoint.loss(p, m0, dt, nsteps, target), rel=1e-10, abs=0)
     assert np.linalg.norm(g_gpu - g_ref) / np.linalg.norm(g_ref) < 1e-6
     mm.mm_destroy(ctx)

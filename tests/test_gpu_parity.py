@@ -134,7 +134,7 @@ def test_exchange_and_effective_field(prec):
     scale = np.sum(np.abs(Eo))
     assert np.max(np.abs(E - Eo)) / scale < TOL[prec]
     tq = mm.mm_max_torque(ctx, md)
-    assert tq == pytest.approx(p.max_torque(m), rel=10 * TOL[prec])
+    assert tq == pytest.approx(p.max_torque(m), rel=10 * TOL[prec], abs=0)
     mm.mm_destroy(ctx)
 
 
@@ -168,7 +168,7 @@ def test_rk4_film64_200_steps_fp64():
         prev = cur
         m = p.rk4_step(m, 1e-13)
     assert worst < 1e-12
-    assert t == pytest.approx(200 * 1e-13, rel=1e-12)
+    assert t == pytest.approx(200 * 1e-13, rel=1e-12, abs=0)
     assert rel_l2(prev, m) < 3e-9
     assert np.max(np.abs(np.linalg.norm(prev, axis=0) - 1)) < 1e-14
     mm.mm_destroy(ctx)
@@ -221,7 +221,7 @@ def test_rkf45_trial_matches_oracle(prec):
     assert rel_l2(host(md), m4) < TOL[prec]
     u = 2.0 ** -53 if prec == mm.MM_F64 else 2.0 ** -24
     assert abs(err - err_o) < 8 * _rkf45_error_bound(p, m, dt, u) + 1e-9 * err_o
-    assert dt_next == pytest.approx(micromag.next_dt(dt, err, 1.0), rel=1e-12)
+    assert dt_next == pytest.approx(micromag.next_dt(dt, err, 1.0), rel=1e-12, abs=0)
     mm.mm_destroy(ctx)
 
 
@@ -234,7 +234,7 @@ def test_rkf45_rejects_then_accepts_fp64():
     t, dt_next, err = mm.mm_llg_step(ctx, md, 0.0, 1e-11, mm.MM_RKF45, tol=1e-5)
     mo, to, dto, erro, rej = micromag.rkf45_step(p, m, 0.0, 1e-11, 1e-5)
     assert rej >= 1
-    assert t == pytest.approx(to, rel=1e-12)
+    assert t == pytest.approx(to, rel=1e-12, abs=0)
     assert err <= 1e-5
     assert rel_l2(host(md), mo) < 1e-12
     mm.mm_destroy(ctx)
@@ -259,7 +259,7 @@ def test_rkf45_trajectory_replayed_by_the_oracle(prec):
         m, err_o = p.rkf45_trial(m, h)
         worst = max(worst, rel_l2(host(md), m))
         assert err <= 1e-5
-        assert dt_next == pytest.approx(micromag.next_dt(h, err, 1e-5), rel=1e-9)
+        assert dt_next == pytest.approx(micromag.next_dt(h, err, 1e-5), rel=1e-9, abs=0)
         t, dt = t_new, dt_next
     assert worst < (1e-12 if prec == mm.MM_F64 else 2e-5), worst
     mm.mm_destroy(ctx)
@@ -286,7 +286,7 @@ def test_relax_film_energy_decreases_fp32():
     E0 = mm.mm_energy(ctx, md).sum()
     t, steps = mm.mm_relax(ctx, md, t_max=2e-11, torque_tol=0.0, max_steps=100000)
     E1 = mm.mm_energy(ctx, md).sum()
-    assert t == pytest.approx(2e-11, rel=1e-9)
+    assert t == pytest.approx(2e-11, rel=1e-9, abs=0)
     assert E1 < E0
     got = host(md)
     assert np.max(np.abs(np.linalg.norm(got, axis=0) - 1)) < 1e-6

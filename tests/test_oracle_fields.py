@@ -40,7 +40,7 @@ def test_demag_is_self_adjoint():
     u, v = unit_random(n, 4), unit_random(n, 5)
     lhs = np.sum(u * p.demag_fft(v))
     rhs = np.sum(p.demag_fft(u) * v)
-    assert lhs == pytest.approx(rhs, rel=1e-12)
+    assert lhs == pytest.approx(rhs, rel=1e-12, abs=0)
 
 
 def test_sampled_direct_sum_matches_full():
@@ -110,7 +110,7 @@ def test_exchange_energy_equals_bond_sum_and_gradient():
     m = unit_random(n, 9)
     m[:, 1, 2, 3] = 0.0
     E = p.energies(m)[1]
-    assert E == pytest.approx(_bond_energy(p, m), rel=1e-12)
+    assert E == pytest.approx(_bond_energy(p, m), rel=1e-12, abs=0)
     # H_ex = -1/(mu0 Ms V) dE/dm for the bond energy (m not constrained)
     H = p.exchange(m)
     for (c, z, y, x) in [(0, 0, 0, 0), (2, 1, 1, 1), (1, 2, 3, 4), (0, 1, 3, 2)]:
@@ -119,7 +119,7 @@ def test_exchange_energy_equals_bond_sum_and_gradient():
         mp_[c, z, y, x] += h
         mm_[c, z, y, x] -= h
         g = (_bond_energy(p, mp_) - _bond_energy(p, mm_)) / (2 * h)
-        assert H[c, z, y, x] == pytest.approx(-g / (MU0 * Ms[z, y, x] * p.V), rel=1e-6)
+        assert H[c, z, y, x] == pytest.approx(-g / (MU0 * Ms[z, y, x] * p.V), rel=1e-6, abs=0)
     assert np.all(H[:, 1, 2, 3] == 0.0)
     assert np.sum(Ms * np.sum(m * H, axis=0)) <= 0.0
 
@@ -129,12 +129,12 @@ def test_anisotropy_energy_limits():
     p = micromag.Problem(n, d, Ku=5e5, u=(0, 0, 1))
     m = np.zeros((3, 2, 3, 4))
     m[2] = 1.0
-    assert p.energies(m)[2] == pytest.approx(-5e5 * p.V * 24, rel=1e-14)
+    assert p.energies(m)[2] == pytest.approx(-5e5 * p.V * 24, rel=1e-14, abs=0)
     m2 = np.zeros_like(m)
     m2[0] = 1.0
     assert p.energies(m2)[2] == 0.0
     H = p.anisotropy(m)
-    assert H[2, 0, 0, 0] == pytest.approx(2 * 5e5 / (MU0 * 8e5), rel=1e-14)
+    assert H[2, 0, 0, 0] == pytest.approx(2 * 5e5 / (MU0 * 8e5), rel=1e-14, abs=0)
 
 
 def test_zeeman_energy():
@@ -143,7 +143,7 @@ def test_zeeman_energy():
     p = micromag.Problem(n, d, h_ext=h)
     m = np.zeros((3, 1, 3, 3))
     m[0] = 1.0
-    assert p.energies(m)[3] == pytest.approx(-MU0 * 8e5 * p.V * 9 * h[0], rel=1e-14)
+    assert p.energies(m)[3] == pytest.approx(-MU0 * 8e5 * p.V * 9 * h[0], rel=1e-14, abs=0)
 
 
 def test_demag_energy_of_uniform_cube():
@@ -152,4 +152,4 @@ def test_demag_energy_of_uniform_cube():
     m = np.zeros((3, 3, 3, 3))
     m[1] = 1.0
     Vt = 27 * p.V
-    assert p.energies(m)[0] == pytest.approx(0.5 * MU0 * 8e5 ** 2 * Vt / 3, rel=1e-12)
+    assert p.energies(m)[0] == pytest.approx(0.5 * MU0 * 8e5 ** 2 * Vt / 3, rel=1e-12, abs=0)

@@ -58,7 +58,7 @@ def test_damping_like_relaxation_closed_form(alpha, eps_prime):
         m = p.rk4_step(m, dt)
     th = np.arccos(np.clip(m[2, 0, 0, 0], -1, 1))
     ref = 2 * np.arctan(np.tan(th0 / 2) * np.exp(-rate * T))
-    assert th == pytest.approx(ref, rel=1e-8)
+    assert th == pytest.approx(ref, rel=1e-8, abs=0)
 
 
 def test_field_like_precession_closed_form():
