@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "mm_internal.cuh"
+#include "mm_tcgen05.cuh"
 
 struct mm_fno {
     int nx, ny, W, M, L, store_bf16, max_batch, device;
@@ -51,6 +52,8 @@ struct mm_fno {
     float2* twy;        // [MY][NY] e^{-2 pi i ky y / NY}
     float* basis;       // [2M][NX] inverse-x basis c_kx (cos, -sin) / (NX NY), c_0 = 1, else 2
     double* red;        // loss reduction scratch [2][B]
+    unsigned char* xbimg;   // tensor-core x transform: twiddle operand image [NX/64][hi, lo][NP x 64] BF16
+    int xNP;            // its N (2M rounded up to 16)
     float out_scale;    // multiply h by this on output (Ms inside relax)
     std::string err;
 };
@@ -416,6 +419,410 @@ inline unsigned wgrad_grid(long P, int B) {
     return (unsigned)(n < 1216 ? n : 1216);
 }
 
+// ------------------------------------------------------- tensor-core GEMMs
+// In the BF16 storage mode the three contractions that dominate the network
+// run on the tensor cores (tcgen05.mma kind::f16, BF16 operands, FP32
+// accumulation in tensor memory): the x transform (rows x NX against the
+// twiddle table), the layer output (per (b, y) row: x against [v ; basis],
+// transposed so the 128 x positions are the MMA's M), and the weight
+// gradients (sum over pixels of dY X^T).  BF16 activations are exact BF16
+// operands; FP32 operands (twiddles, basis, weights, spectra, cotangents)
+// are split into hi + lo BF16 parts and the products hi.hi + hi.lo + lo.hi
+// are accumulated, which keeps about 16 bits of each, well above the BF16
+// storage of the activations.  Tiles: M = 128 rows, K in chunks of 64
+// (16 per instruction), operands staged by the block's threads in the
+// canonical K-major layout; one thread issues the MMAs, the block waits on
+// the commit with a bounded poll and reads the accumulator with tcgen05.ld.
+// A wait that gives up raises g_fno_status (read back by the synchronising
+// FNO calls) and the block frees its tensor memory and returns.
+constexpr int kTcM = 128, kTcKC = 64;
+constexpr long kFnoWaitLimit = 1L << 22;
+__device__ int g_fno_status;
+
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// 8 BF16 values as one 16-byte word
+__device__ __forceinline__ uint4 pack8(const __nv_bfloat16 (&v)[8]) {
+    uint4 r;
+    r.x = (uint32_t)__bfloat16_as_ushort(v[0]) | ((uint32_t)__bfloat16_as_ushort(v[1]) << 16);
+    r.y = (uint32_t)__bfloat16_as_ushort(v[2]) | ((uint32_t)__bfloat16_as_ushort(v[3]) << 16);
+    r.z = (uint32_t)__bfloat16_as_ushort(v[4]) | ((uint32_t)__bfloat16_as_ushort(v[5]) << 16);
+    r.w = (uint32_t)__bfloat16_as_ushort(v[6]) | ((uint32_t)__bfloat16_as_ushort(v[7]) << 16);
+    return r;
+}
+
+// twiddle operand of the tensor-core x transform: chunk c, part (hi, lo),
+// row n = 2 kx + (0: Re, 1: Im) of e^{-2 pi i kx x / NX}, column x - 64 c;
+// rows n >= 2M are zero
+__global__ void k_init_xbimg(unsigned char* __restrict__ img, int NX, int M, int NP) {
+    const long total = (long)(NX / kTcKC) * NP * kTcKC;
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const int c = (int)(idx / (NP * kTcKC)), e = (int)(idx % (NP * kTcKC));
+        const int n = e / kTcKC, k = e % kTcKC;
+        const int x = c * kTcKC + k, kx = n >> 1;
+        double v = 0.0;
+        if (n < 2 * M) {
+            double sn, cs;
+            sincospi(2.0 * (double)(((long)kx * x) % NX) / (double)NX, &sn, &cs);
+            v = (n & 1) ? -sn : cs;
+        }
+        const __nv_bfloat16 hi = __float2bfloat16_rn((float)v);
+        const __nv_bfloat16 lo = __float2bfloat16_rn((float)(v - (double)__bfloat162float(hi)));
+        unsigned char* base = img + (long)c * 2 * NP * kTcKC * 2;
+        const int o = tc5::kmajor_off<2>(n, k, kTcKC);
+        *reinterpret_cast<__nv_bfloat16*>(base + o) = hi;
+        *reinterpret_cast<__nv_bfloat16*>(base + NP * kTcKC * 2 + o) = lo;
+    }
+}
+
+// A[row][kx] = scale(kx) sum_x X[row][x] e^{-2 pi i kx x / NX} on the tensor
+// cores; NX a multiple of 64, one block per 128 rows, NP = 2M rounded up
+// to 16.  SI = BF16 (activations, exact) or float (cotangents, split).
+template <typename SI, int NP>
+__global__ void __launch_bounds__(128) k_dft_x_tc(const SI* __restrict__ X, float2* __restrict__ A,
+                                                  const unsigned char* __restrict__ bimg, long rows, int NX, int M,
+                                                  float scale0, float scale1) {
+    constexpr bool SPLIT = std::is_same<SI, float>::value;
+    constexpr int A_BYTES = kTcM * kTcKC * 2, B_BYTES = NP * kTcKC * 2;
+    constexpr uint32_t NCOL = NP <= 32 ? 32 : 64;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* a_hi = smem;
+    unsigned char* a_lo = smem + A_BYTES;
+    unsigned char* b_hi = smem + 2 * A_BYTES;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(b_hi + 2 * B_BYTES);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(b_hi + 2 * B_BYTES + 16);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(mbar);
+    if (warp == 0) tc5::tmem_alloc(slot, NCOL);
+    if (tid == 0) tc5::mbar_init(mb, 1);
+    tc5::fence_before_sync();
+    __syncthreads();
+    tc5::fence_after_sync();
+    const uint32_t tmem = *slot;
+    const long r0 = (long)blockIdx.x * kTcM;
+    const int nch = NX / kTcKC;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int c = 0; c < nch && ok; ++c) {
+        for (int e = tid; e < kTcM * 8; e += blockDim.x) {
+            const int r = e >> 3, ch = e & 7;
+            const long row = r0 + r;
+            const int o = tc5::kmajor_off<2>(r, ch * 8, kTcKC);
+            if constexpr (SPLIT) {
+                float f[8];
+                if (row < rows) {
+                    const float4 f0 = *reinterpret_cast<const float4*>(X + row * NX + c * kTcKC + ch * 8);
+                    const float4 f1 = *reinterpret_cast<const float4*>(X + row * NX + c * kTcKC + ch * 8 + 4);
+                    f[0] = f0.x; f[1] = f0.y; f[2] = f0.z; f[3] = f0.w;
+                    f[4] = f1.x; f[5] = f1.y; f[6] = f1.z; f[7] = f1.w;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) f[i] = 0.f;
+                }
+                __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) split_bf16(f[i], hi[i], lo[i]);
+                *reinterpret_cast<uint4*>(a_hi + o) = pack8(hi);
+                *reinterpret_cast<uint4*>(a_lo + o) = pack8(lo);
+            } else {
+                const uint4 w = row < rows ? *reinterpret_cast<const uint4*>(X + row * NX + c * kTcKC + ch * 8)
+                                           : make_uint4(0u, 0u, 0u, 0u);
+                *reinterpret_cast<uint4*>(a_hi + o) = w;
+            }
+        }
+        {
+            const uint4* src = reinterpret_cast<const uint4*>(bimg + (long)c * 2 * B_BYTES);
+            uint4* dst = reinterpret_cast<uint4*>(b_hi);
+            for (int e = tid; e < 2 * B_BYTES / 16; e += blockDim.x) dst[e] = src[e];
+        }
+        tc5::fence_async_smem();
+        tc5::fence_before_sync();
+        __syncthreads();
+        tc5::fence_after_sync();
+        if (tid == 0) {
+            constexpr uint32_t id = tc5::idesc(false, kTcM, NP);
+            constexpr uint32_t sbo = (kTcKC / 8) * 128;
+            const uint32_t ah = (uint32_t)__cvta_generic_to_shared(a_hi), al = (uint32_t)__cvta_generic_to_shared(a_lo);
+            const uint32_t bh = (uint32_t)__cvta_generic_to_shared(b_hi), bl = bh + B_BYTES;
+#pragma unroll
+            for (int kc = 0; kc < kTcKC / 16; ++kc) {
+                const uint64_t dah = tc5::smem_desc(ah + kc * 256, 128, sbo);
+                const uint64_t dbh = tc5::smem_desc(bh + kc * 256, 128, sbo);
+                tc5::mma_bf16(tmem, dah, dbh, id, (c > 0 || kc > 0) ? 1u : 0u);
+                tc5::mma_bf16(tmem, dah, tc5::smem_desc(bl + kc * 256, 128, sbo), id, 1u);
+                if constexpr (SPLIT) tc5::mma_bf16(tmem, tc5::smem_desc(al + kc * 256, 128, sbo), dbh, id, 1u);
+            }
+            tc5::commit(mb);
+        }
+        const bool got = tc5::mbar_wait(mb, phase, kFnoWaitLimit);
+        phase ^= 1u;
+        tc5::fence_after_sync();
+        ok = __syncthreads_and(got) != 0;       // the same decision in every thread
+    }
+    if (ok) {
+        const long row = r0 + tid;
+#pragma unroll
+        for (int cc = 0; cc < NP / 16; ++cc) {
+            float v[16];
+            tc5::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cc * 16, v);
+            if (row < rows) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int kx = cc * 8 + j;
+                    if (kx < M) {
+                        const float sc = kx == 0 ? scale0 : scale1;
+                        A[row * M + kx] = make_float2(v[2 * j] * sc, v[2 * j + 1] * sc);
+                    }
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicCAS(&g_fno_status, 0, (int)MM_ERR_TIMEOUT);
+    }
+    tc5::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc5::tmem_free(tmem, NCOL);
+}
+
+// layer output on the tensor cores for one (b, y) row and 128 x positions
+// (NX a multiple of 128), the transposed form of k_layer_out's GEMM:
+//   a[co][x] = bias[co] + sum_k Aop[x][k] Bop[co][k],
+//   Aop = [v rows ; basis rows]^T (K = W + 2M padded to KP, a multiple of 16),
+//   Bop = [W | Re U, Im U],
+// then v_next = GELU(a) (or a for the last layer).  N = 32 (rows co >= W zero).
+__global__ void __launch_bounds__(128) k_layer_out_tc(const __nv_bfloat16* __restrict__ v, const float2* __restrict__ U,
+                                                      const float* __restrict__ Wt, const float* __restrict__ bias,
+                                                      const float* __restrict__ basis, __nv_bfloat16* __restrict__ a_out,
+                                                      __nv_bfloat16* __restrict__ v_next, int W, int NY, int NX, int M,
+                                                      int KP, int last) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int A_BYTES = kTcM * KP * 2, B_BYTES = 32 * KP * 2;
+    unsigned char* a_hi = smem;
+    unsigned char* a_lo = smem + A_BYTES;
+    unsigned char* b_hi = smem + 2 * A_BYTES;
+    unsigned char* b_lo = b_hi + B_BYTES;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(b_lo + B_BYTES);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(b_lo + B_BYTES + 16);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int y = blockIdx.x, b = blockIdx.y, x0 = blockIdx.z * kTcM;
+    const long P = (long)NY * NX;
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(mbar);
+    if (warp == 0) tc5::tmem_alloc(slot, 32);
+    if (tid == 0) tc5::mbar_init(mb, 1);
+    // A: thread tid owns row x = x0 + tid
+    {
+        const int x = x0 + tid;
+        for (int k8 = 0; k8 < KP; k8 += 8) {
+            __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int k = k8 + i;
+                if (k < W) {
+                    hi[i] = v[((long)b * W + k) * P + (long)y * NX + x];
+                    lo[i] = __float2bfloat16_rn(0.f);
+                } else if (k < W + 2 * M) {
+                    split_bf16(basis[(long)(k - W) * NX + x], hi[i], lo[i]);
+                } else {
+                    hi[i] = lo[i] = __float2bfloat16_rn(0.f);
+                }
+            }
+            const int o = tc5::kmajor_off<2>(tid, k8, KP);
+            *reinterpret_cast<uint4*>(a_hi + o) = pack8(hi);
+            *reinterpret_cast<uint4*>(a_lo + o) = pack8(lo);
+        }
+    }
+    // B: [co][k], 32 rows
+    for (int e = tid; e < 32 * (KP / 8); e += blockDim.x) {
+        const int co = e / (KP / 8), k8 = (e % (KP / 8)) * 8;
+        __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int k = k8 + i;
+            float val = 0.f;
+            if (co < W) {
+                if (k < W) {
+                    val = Wt[co * W + k];
+                } else if (k < W + 2 * M) {
+                    const float2 u = U[(((long)b * W + co) * NY + y) * M + ((k - W) >> 1)];
+                    val = ((k - W) & 1) ? u.y : u.x;
+                }
+            }
+            split_bf16(val, hi[i], lo[i]);
+        }
+        const int o = tc5::kmajor_off<2>(co, k8, KP);
+        *reinterpret_cast<uint4*>(b_hi + o) = pack8(hi);
+        *reinterpret_cast<uint4*>(b_lo + o) = pack8(lo);
+    }
+    tc5::fence_async_smem();
+    tc5::fence_before_sync();
+    __syncthreads();
+    tc5::fence_after_sync();
+    const uint32_t tmem = *slot;
+    if (tid == 0) {
+        const uint32_t id = tc5::idesc(false, kTcM, 32);
+        const uint32_t sbo = (uint32_t)(KP / 8) * 128;
+        const uint32_t ah = (uint32_t)__cvta_generic_to_shared(a_hi), al = (uint32_t)__cvta_generic_to_shared(a_lo);
+        const uint32_t bh = (uint32_t)__cvta_generic_to_shared(b_hi), bl = (uint32_t)__cvta_generic_to_shared(b_lo);
+        for (int kc = 0; kc < KP / 16; ++kc) {
+            const uint64_t dah = tc5::smem_desc(ah + kc * 256, 128, sbo), dbh = tc5::smem_desc(bh + kc * 256, 128, sbo);
+            tc5::mma_bf16(tmem, dah, dbh, id, kc > 0 ? 1u : 0u);
+            tc5::mma_bf16(tmem, dah, tc5::smem_desc(bl + kc * 256, 128, sbo), id, 1u);
+            tc5::mma_bf16(tmem, tc5::smem_desc(al + kc * 256, 128, sbo), dbh, id, 1u);
+        }
+        tc5::commit(mb);
+    }
+    const bool got = tc5::mbar_wait(mb, 0, kFnoWaitLimit);
+    tc5::fence_after_sync();
+    const bool ok = __syncthreads_and(got) != 0;
+    if (ok) {
+        const int x = x0 + tid;
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            float d[16];
+            tc5::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cc * 16, d);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int co = cc * 16 + j;
+                if (co < W) {
+                    const float val = d[j] + bias[co];
+                    const long o = ((long)b * W + co) * P + (long)y * NX + x;
+                    a_out[o] = __float2bfloat16_rn(val);
+                    v_next[o] = __float2bfloat16_rn(last ? val : gelu(val));
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicCAS(&g_fno_status, 0, (int)MM_ERR_TIMEOUT);
+    }
+    tc5::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc5::tmem_free(tmem, 32);
+}
+
+inline size_t layer_out_tc_smem(int KP) { return (size_t)2 * kTcM * KP * 2 + (size_t)2 * 32 * KP * 2 + 64; }
+
+// dW[co][ci] += sum_{b,p} dY[b][co][p] X[b][ci][p], db[co] += sum dY, on the
+// tensor cores: M = 128 rows of which the first Co (<= 32) are dY's
+// channels (split hi + lo), N = NP >= Ci + 1 columns of X's channels plus a
+// column of ones (the bias), K = 64 pixels per step; blocks walk the
+// pixel chunks of all samples (P a multiple of 64) and add their sums once.
+template <typename SX, int NP>
+__global__ void __launch_bounds__(128) k_wgrad_tc(const float* __restrict__ dY, const SX* __restrict__ X,
+                                                  float* __restrict__ dW, float* __restrict__ db, int Co, int Ci,
+                                                  long P, int B) {
+    constexpr bool SPLITX = std::is_same<SX, float>::value;
+    constexpr int A_BYTES = kTcM * kTcKC * 2, B_BYTES = NP * kTcKC * 2;
+    constexpr uint32_t NCOL = NP <= 32 ? 32 : 64;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* a_hi = smem;
+    unsigned char* a_lo = smem + A_BYTES;
+    unsigned char* b_hi = smem + 2 * A_BYTES;
+    unsigned char* b_lo = b_hi + B_BYTES;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(b_lo + B_BYTES);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(b_lo + B_BYTES + 16);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(mbar);
+    if (warp == 0) tc5::tmem_alloc(slot, NCOL);
+    if (tid == 0) tc5::mbar_init(mb, 1);
+    // zero both operands once: rows co >= Co of A and columns beyond Ci of B
+    // stay zero, the bias column is set below
+    for (int e = tid; e < (2 * A_BYTES + 2 * B_BYTES) / 16; e += blockDim.x)
+        reinterpret_cast<uint4*>(smem)[e] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    for (int e = tid; e < kTcKC; e += blockDim.x)
+        *reinterpret_cast<__nv_bfloat16*>(b_hi + tc5::kmajor_off<2>(Ci, e, kTcKC)) = __float2bfloat16_rn(1.f);
+    tc5::fence_before_sync();
+    __syncthreads();
+    tc5::fence_after_sync();
+    const uint32_t tmem = *slot;
+    const long cps = P / kTcKC;
+    uint32_t phase = 0;
+    bool ok = true, any = false;
+    for (long c = blockIdx.x; c < (long)B * cps && ok; c += gridDim.x) {
+        const int b = (int)(c / cps);
+        const long p0 = (c % cps) * kTcKC;
+        for (int e = tid; e < Co * 8; e += blockDim.x) {
+            const int co = e >> 3, ch = e & 7;
+            const float* src = dY + ((long)b * Co + co) * P + p0 + ch * 8;
+            const float4 f0 = *reinterpret_cast<const float4*>(src), f1 = *reinterpret_cast<const float4*>(src + 4);
+            const float f[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+            __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) split_bf16(f[i], hi[i], lo[i]);
+            const int o = tc5::kmajor_off<2>(co, ch * 8, kTcKC);
+            *reinterpret_cast<uint4*>(a_hi + o) = pack8(hi);
+            *reinterpret_cast<uint4*>(a_lo + o) = pack8(lo);
+        }
+        for (int e = tid; e < Ci * 8; e += blockDim.x) {
+            const int ci = e >> 3, ch = e & 7;
+            const int o = tc5::kmajor_off<2>(ci, ch * 8, kTcKC);
+            if constexpr (SPLITX) {
+                const float* src = X + ((long)b * Ci + ci) * P + p0 + ch * 8;
+                const float4 f0 = *reinterpret_cast<const float4*>(src), f1 = *reinterpret_cast<const float4*>(src + 4);
+                const float f[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+                __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) split_bf16(f[i], hi[i], lo[i]);
+                *reinterpret_cast<uint4*>(b_hi + o) = pack8(hi);
+                *reinterpret_cast<uint4*>(b_lo + o) = pack8(lo);
+            } else {
+                *reinterpret_cast<uint4*>(b_hi + o) =
+                    *reinterpret_cast<const uint4*>(X + ((long)b * Ci + ci) * P + p0 + ch * 8);
+            }
+        }
+        tc5::fence_async_smem();
+        tc5::fence_before_sync();
+        __syncthreads();
+        tc5::fence_after_sync();
+        if (tid == 0) {
+            constexpr uint32_t id = tc5::idesc(false, kTcM, NP);
+            constexpr uint32_t sbo = (kTcKC / 8) * 128;
+            const uint32_t ah = (uint32_t)__cvta_generic_to_shared(a_hi), al = (uint32_t)__cvta_generic_to_shared(a_lo);
+            const uint32_t bh = (uint32_t)__cvta_generic_to_shared(b_hi), bl = (uint32_t)__cvta_generic_to_shared(b_lo);
+#pragma unroll
+            for (int kc = 0; kc < kTcKC / 16; ++kc) {
+                const uint64_t dbh = tc5::smem_desc(bh + kc * 256, 128, sbo);
+                const uint64_t dah = tc5::smem_desc(ah + kc * 256, 128, sbo);
+                tc5::mma_bf16(tmem, dah, dbh, id, (any || kc > 0) ? 1u : 0u);
+                tc5::mma_bf16(tmem, tc5::smem_desc(al + kc * 256, 128, sbo), dbh, id, 1u);
+                if constexpr (SPLITX) tc5::mma_bf16(tmem, dah, tc5::smem_desc(bl + kc * 256, 128, sbo), id, 1u);
+            }
+            tc5::commit(mb);
+        }
+        any = true;
+        const bool got = tc5::mbar_wait(mb, phase, kFnoWaitLimit);
+        phase ^= 1u;
+        tc5::fence_after_sync();
+        ok = __syncthreads_and(got) != 0;
+    }
+    if (ok && any && warp == 0) {
+#pragma unroll
+        for (int cc = 0; cc < NP / 16; ++cc) {
+            float d[16];
+            tc5::tmem_ld16(tmem + cc * 16, d);
+            const int co = tid;
+            if (co < Co) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int ci = cc * 16 + j;
+                    if (ci < Ci) atomicAdd(&dW[co * Ci + ci], d[j]);
+                    else if (ci == Ci) atomicAdd(&db[co], d[j]);
+                }
+            }
+        }
+    } else if (!ok && tid == 0) {
+        atomicCAS(&g_fno_status, 0, (int)MM_ERR_TIMEOUT);
+    }
+    tc5::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc5::tmem_free(tmem, NCOL);
+}
+
+template <int NP> constexpr size_t gemm_tc_smem() { return (size_t)2 * kTcM * kTcKC * 2 + (size_t)2 * NP * kTcKC * 2 + 64; }
+
 // per-sample sums of (h - t)^2 and t^2
 __global__ void k_loss_sums(const float* __restrict__ h, const float* __restrict__ t, double* __restrict__ red, long n) {
     const int b = blockIdx.y;
@@ -500,6 +907,57 @@ int ffail(mm_fno* f, int code, const char* msg) {
     return fail(nullptr, code, "%s", msg);
 }
 
+inline int round16(int v) { return (v + 15) / 16 * 16; }
+
+// after a synchronisation: TIMEOUT if a tensor-core wait gave up since the
+// last check (the flag is cleared), else OK
+int tc_status(mm_fno* f) {
+    int st = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&st, g_fno_status, sizeof(int));
+    if (e != cudaSuccess) return ffail(f, MM_ERR_CUDA, cudaGetErrorString(e));
+    if (st) {
+        const int zero = 0;
+        cudaMemcpyToSymbol(g_fno_status, &zero, sizeof(int));
+        return ffail(f, st, "a tensor-core wait of the FNO kernels gave up (TIMEOUT)");
+    }
+    return MM_OK;
+}
+
+// x transform rows x NX -> A (tensor cores when the operand image exists)
+template <typename SI>
+void dft_x(mm_fno* f, const SI* X, float2* out, long rows, float scale0, float scale1) {
+    if (f->xbimg) {
+        const unsigned g = (unsigned)((rows + kTcM - 1) / kTcM);
+        switch (f->xNP) {
+            case 16: k_dft_x_tc<SI, 16><<<g, 128, gemm_tc_smem<16>(), f->stream>>>(X, out, f->xbimg, rows, f->nx, f->M, scale0, scale1); return;
+            case 32: k_dft_x_tc<SI, 32><<<g, 128, gemm_tc_smem<32>(), f->stream>>>(X, out, f->xbimg, rows, f->nx, f->M, scale0, scale1); return;
+            case 48: k_dft_x_tc<SI, 48><<<g, 128, gemm_tc_smem<48>(), f->stream>>>(X, out, f->xbimg, rows, f->nx, f->M, scale0, scale1); return;
+            default: k_dft_x_tc<SI, 64><<<g, 128, gemm_tc_smem<64>(), f->stream>>>(X, out, f->xbimg, rows, f->nx, f->M, scale0, scale1); return;
+        }
+    }
+    k_dft_x<SI><<<(unsigned)((rows + kDxRows - 1) / kDxRows), 256, 0, f->stream>>>(X, out, f->twx, rows, f->nx, f->M,
+                                                                                  scale0, scale1);
+}
+
+// weight gradients of a 1x1 map (tensor cores in the BF16 mode when the
+// pixel count is a multiple of 64)
+template <typename SX>
+void wgrad(mm_fno* f, const float* dY, const SX* X, float* dW, float* db, int Co, int Ci, int B) {
+    const long P = f->P;
+    if (f->store_bf16 && P % kTcKC == 0) {
+        const long chunks = (long)B * (P / kTcKC);
+        const unsigned g = (unsigned)(chunks < 608 ? chunks : 608);
+        if (round16(Ci + 1) <= 16)
+            k_wgrad_tc<SX, 16><<<g, 128, gemm_tc_smem<16>(), f->stream>>>(dY, X, dW, db, Co, Ci, P, B);
+        else if (round16(Ci + 1) <= 32)
+            k_wgrad_tc<SX, 32><<<g, 128, gemm_tc_smem<32>(), f->stream>>>(dY, X, dW, db, Co, Ci, P, B);
+        else
+            k_wgrad_tc<SX, 48><<<g, 128, gemm_tc_smem<48>(), f->stream>>>(dY, X, dW, db, Co, Ci, P, B);
+        return;
+    }
+    k_wgrad<SX><<<wgrad_grid(P, B), 256, 0, f->stream>>>(dY, X, dW, db, Co, Ci, P, B);
+}
+
 #define FNO_CHECK(f)                                                                           \
     do {                                                                                       \
         cudaError_t e_ = cudaGetLastError();                                                   \
@@ -518,11 +976,20 @@ template <typename SS> int forward_t(mm_fno* f, const float* m, float* h, int B)
     for (int l = 0; l < f->L; ++l) {
         SS* vl = v + l * vs;
         float2* S = f->S + (long)l * f->max_batch * W * K;
-        k_dft_x<SS><<<(unsigned)(((long)B * W * NY + kDxRows - 1) / kDxRows), 256, 0, f->stream>>>(
-            vl, f->A, f->twx, (long)B * W * NY, NX, M, 1.f, 1.f);
+        dft_x<SS>(f, vl, f->A, (long)B * W * NY, 1.f, 1.f);
         k_dft_y_modes<<<g1(8L * B * W * 2 * M * M), kFT, 0, f->stream>>>(f->A, S, f->twy, B * W, NY, M, -1.f);
         k_mix<<<g1((long)B * W * K), kFT, 0, f->stream>>>(S, (const float2*)(f->params + f->o_R[l]), f->T, B, W, K, 0);
         k_dft_y<<<g1((long)B * W * NY * M), kFT, 0, f->stream>>>(f->T, f->U, f->twy, B * W, NY, M, 0, 1.f);
+        if constexpr (std::is_same<SS, __nv_bfloat16>::value) {
+            if (NX % kTcM == 0) {
+                const int KP = round16(W + 2 * M);
+                k_layer_out_tc<<<dim3((unsigned)NY, (unsigned)B, (unsigned)(NX / kTcM)), 128, layer_out_tc_smem(KP),
+                                 f->stream>>>(vl, f->U, f->params + f->o_W[l], f->params + f->o_b[l], f->basis,
+                                              a + l * vs, v + (l + 1) * vs, W, NY, NX, M, KP, l == f->L - 1);
+                FNO_CHECK(f);
+                continue;
+            }
+        }
         k_layer_out<SS><<<dim3((unsigned)NY, (unsigned)B, (unsigned)((NX + kLoTile - 1) / kLoTile)), 256,
                           layer_out_smem(W, M), f->stream>>>(vl, f->U, f->params + f->o_W[l], f->params + f->o_b[l],
                                                              f->basis, a + l * vs, v + (l + 1) * vs, B, W, NY, NX, M,
@@ -545,7 +1012,7 @@ template <typename SS> int backward_t(mm_fno* f, const float* dh, int B) {
     float* dv2 = dv + vs;
     float* G = f->grads;
     // projection: dQ += dh v_L^T, dq += sum dh, dv_L = Q^T dh
-    k_wgrad<SS><<<wgrad_grid(P, B), 256, 0, f->stream>>>(dh, v + f->L * vs, G + f->o_Q, G + f->o_q, 3, W, P, B);
+    wgrad<SS>(f, dh, v + f->L * vs, G + f->o_Q, G + f->o_q, 3, W, B);
     k_chan<float, float><<<g1((long)B * P), kFT, 0, f->stream>>>(dh, f->params + f->o_Q, nullptr, dv, 3, W, P, B, 1.f, 1);
     FNO_CHECK(f);
     for (int l = f->L - 1; l >= 0; --l) {
@@ -554,12 +1021,11 @@ template <typename SS> int backward_t(mm_fno* f, const float* dh, int B) {
         // da = dv * GELU'(a)
         k_gelu_bwd<SS><<<g1((long)B * W * P), kFT, 0, f->stream>>>(dv, a + l * vs, (long)B * W * P, l == f->L - 1);
         // channel part
-        k_wgrad<SS><<<wgrad_grid(P, B), 256, 0, f->stream>>>(dv, vl, G + f->o_W[l], G + f->o_b[l], W, W, P, B);
+        wgrad<SS>(f, dv, vl, G + f->o_W[l], G + f->o_b[l], W, W, B);
         k_chan<float, float><<<g1((long)B * P), kFT, 0, f->stream>>>(dv, f->params + f->o_W[l], nullptr, dv2, W, W, P, B,
                                                                      1.f, 1);
         // spectral part: dU = c / P sum_x da e^{-i theta}
-        k_dft_x<float><<<(unsigned)(((long)B * W * NY + kDxRows - 1) / kDxRows), 256, 0, f->stream>>>(
-            dv, f->U, f->twx, (long)B * W * NY, NX, M, 1.f / (float)P, 2.f / (float)P);
+        dft_x<float>(f, dv, f->U, (long)B * W * NY, 1.f / (float)P, 2.f / (float)P);
         k_dft_y_modes<<<g1(8L * B * W * 2 * M * M), kFT, 0, f->stream>>>(f->U, f->T, f->twy, B * W, NY, M, -1.f);
         k_mix_grad<<<g1((long)W * W * K), kFT, 0, f->stream>>>(f->T, S, (float2*)(G + f->o_R[l]), B, W, K);
         // dS = R^H dT into U (free again; the stored spectra S stay intact for a later backward)
@@ -649,6 +1115,8 @@ int mm_fno_create(mm_fno** out, int nx, int ny, int width, int modes, int layers
     A((void**)&f->twy, (size_t)2 * modes * ny * sizeof(float2));
     A((void**)&f->basis, (size_t)2 * modes * nx * sizeof(float));
     A((void**)&f->red, (size_t)2 * max_batch * sizeof(double));
+    f->xNP = (2 * modes + 15) / 16 * 16;
+    if (f->store_bf16 && nx % kTcKC == 0) A((void**)&f->xbimg, (size_t)(nx / kTcKC) * 2 * f->xNP * kTcKC * 2);
     if (!ok) {
         cudaGetLastError();
         mm_fno_destroy(f);
@@ -674,7 +1142,17 @@ int mm_fno_create(mm_fno** out, int nx, int ny, int width, int modes, int layers
     if (ce == cudaSuccess) ce = cudaMemset(f->adam_v, 0, o * 4);
     k_init_tw<<<64, 256, 0, f->stream>>>(f->twx, f->twy, nx, ny, modes);
     k_init_basis<<<64, 256, 0, f->stream>>>(f->twx, f->basis, nx, ny, modes);
+    if (f->xbimg) k_init_xbimg<<<64, 256, 0, f->stream>>>(f->xbimg, nx, modes, f->xNP);
     if (ce == cudaSuccess) ce = cudaGetLastError();
+    if (ce == cudaSuccess)
+        ce = cudaFuncSetAttribute(k_layer_out_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)layer_out_tc_smem(round16(32 + 2 * kMaxModes)));
+    if (ce == cudaSuccess)
+        ce = cudaFuncSetAttribute(k_dft_x_tc<__nv_bfloat16, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)gemm_tc_smem<64>());
+    if (ce == cudaSuccess)
+        ce = cudaFuncSetAttribute(k_dft_x_tc<float, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)gemm_tc_smem<64>());
     // the layer-output GEMM keeps its K x 256 operand in dynamic shared memory
     if (ce == cudaSuccess)
         ce = cudaFuncSetAttribute(k_layer_out<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -696,7 +1174,7 @@ void mm_fno_destroy(mm_fno* f) {
     cudaSetDevice(f->device);
     cudaStreamSynchronize(f->stream);
     void* ptrs[] = {f->params, f->grads, f->adam_m, f->adam_v, f->v,   f->a,     f->S,  f->A,
-                    f->T,      f->U,     f->dv,     f->twx,    f->twy, f->basis, f->red};
+                    f->T,      f->U,     f->dv,     f->twx,    f->twy, f->basis, f->red, f->xbimg};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete f;
@@ -720,8 +1198,7 @@ int mm_fno_backward(mm_fno* f, const void* m, const void* dh, int batch) {
     // lift: dP += dv_0 m^T, dp += sum dv_0 (dv_0 ends in the buffer the last swap selected)
     const long vs = (long)f->max_batch * f->W * f->P;
     float* dv0 = (float*)f->dv + ((f->L % 2) ? vs : 0);
-    k_wgrad<float><<<wgrad_grid(f->P, batch), 256, 0, f->stream>>>(dv0, (const float*)m, f->grads + f->o_P,
-                                                                    f->grads + f->o_p, f->W, 3, f->P, batch);
+    wgrad<float>(f, dv0, (const float*)m, f->grads + f->o_P, f->grads + f->o_p, f->W, 3, batch);
     FNO_CHECK(f);
     return MM_OK;
 }
@@ -758,6 +1235,8 @@ int mm_fno_loss(mm_fno* f, const void* h, const void* target, void* dh, int batc
         e = cudaMemcpyAsync(r.data(), f->red, 2 * batch * sizeof(double), cudaMemcpyDeviceToHost, f->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
         if (e != cudaSuccess) return ffail(f, MM_ERR_CUDA, cudaGetErrorString(e));
+        int rc = tc_status(f);
+        if (rc) return rc;
         double L = 0;
         for (int b = 0; b < batch; ++b) L += r[2 * b] / r[2 * b + 1];
         *loss_out = L / batch;
@@ -769,6 +1248,10 @@ int mm_fno_params(mm_fno* f, float* host_params, float* host_grads, const float*
     if (!f) return fail(nullptr, MM_ERR_INVALID_ARG, "fno is NULL");
     cudaSetDevice(f->device);
     cudaError_t e = cudaStreamSynchronize(f->stream);
+    if (e == cudaSuccess) {
+        int rc = tc_status(f);
+        if (rc) return rc;
+    }
     if (e == cudaSuccess && host_set) e = cudaMemcpy(f->params, host_set, f->nparams * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && host_params) e = cudaMemcpy(host_params, f->params, f->nparams * 4, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && host_grads) e = cudaMemcpy(host_grads, f->grads, f->nparams * 4, cudaMemcpyDeviceToHost);

@@ -56,9 +56,10 @@ def sample_m(B, NY, NX, seed):
     return np.stack(ms).astype(np.float32)
 
 
-CASES = [  # (NY, NX, W, M, L, B)
+CASES = [  # (NY, NX, W, M, L, B); NX = 128 takes the tensor-core contractions in the BF16 mode
     (32, 32, 8, 4, 3, 2),
     (24, 40, 5, 6, 2, 3),
+    (64, 128, 16, 8, 2, 2),
 ]
 
 
@@ -85,7 +86,7 @@ def test_forward_and_gradients_match_oracle(case, bf16):
     mm.mm_fno_backward(f, md, dh)
     _, g = mm.mm_fno_params(f)
     L_ref, g_ref = ofno.loss_and_grad(params.astype(np.float64), m, target, W, M, L)
-    assert loss == pytest.approx(L_ref, rel=2e-2 if bf16 else 1e-5)
+    assert loss == pytest.approx(L_ref, rel=2e-2 if bf16 else 1e-5, abs=0)
     for name, sl in blocks(W, M, L):
         e = np.linalg.norm(g[sl] - g_ref[sl]) / np.linalg.norm(g_ref[sl])
         assert e < (5e-2 if bf16 else 1e-4), (name, e)
@@ -189,7 +190,7 @@ def test_relax_falls_back_to_exact_field_above_the_bound():
     m_ref = m0.clone()
     mm.mm_relax(ctx, m_ref, 5e-9, 1e-2)
     E, E_ref = mm.mm_energy(ctx, m), mm.mm_energy(ctx, m_ref)
-    assert sum(E) == pytest.approx(sum(E_ref), rel=1e-3)
+    assert sum(E) == pytest.approx(sum(E_ref), rel=1e-3, abs=0)
     assert mm.mm_max_torque(ctx, m) <= 1e-2
     mm.mm_fno_destroy(f)
     mm.mm_destroy(ctx)
