@@ -51,8 +51,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["f32", "f64"], default="f32")
-    ap.add_argument("--fft-mode", choices=["fp32", "tf32", "bf16", "ff"], default="fp32",
-                    help="tf32/bf16: tensor-core split-precision y passes (f32); ff: float-float demag passes (f64)")
+    ap.add_argument("--fft-mode", choices=["fp32", "tf32", "bf16", "ff", "f4"], default="fp32",
+                    help="tf32/bf16: tensor-core split-precision y passes (f32); ff: float-float demag passes (f64); "
+                         "f4: y forward, z product and y inverse fused over kx planes in 4-CTA clusters (f32)")
     ap.add_argument("--workload", choices=["film512"], default="film512")
     ap.add_argument("--solver", choices=["relax", "bb"], default="relax",
                     help="relax: adaptive RKF45 (default); bb: Barzilai-Borwein minimiser iterations")
@@ -728,6 +729,8 @@ def run_ours(args):
         if prec != mm.MM_F64:
             raise SystemExit("--fft-mode ff needs --precision f64")
         mm.mm_set_fft_mode(ctx, mm.MM_FFT_FF)
+    elif args.fft_mode == "f4":
+        mm.mm_set_fft_mode(ctx, mm.MM_FFT_F4)
     elif args.fft_mode != "fp32":
         mm.mm_set_fft_mode(ctx, mm.MM_TC_TF32 if args.fft_mode == "tf32" else mm.MM_TC_BF16)
     if args.dmi:

@@ -299,7 +299,7 @@ int mm_rk4_trajectory_vjp(mm_ctx* ctx, const void* m0, double dt, long nsteps, v
  * 5th-generation tensor cores, FP32 operands split into hi + lo parts of the
  * tensor-core type and multiplied as hi.hi + hi.lo + lo.hi with FP32
  * accumulation (about 21 significant bits for TF32, 16 for BF16). */
-enum { MM_TC_TF32 = 1, MM_TC_BF16 = 2, MM_FFT_FF = 3 };
+enum { MM_TC_TF32 = 1, MM_TC_BF16 = 2, MM_FFT_FF = 3, MM_FFT_F4 = 4 };
 
 /* out[l][k] = sum_n in[l][n] exp(direction 2 pi i n k / 32) for nlines
  * lines of 32 complex FP32 values (interleaved re, im; device arrays,
@@ -313,7 +313,9 @@ int mm_dft32_tc(const void* in, void* out, long nlines, int mode, int direction,
  * evaluates its transforms).  0 = the context's own precision (default).
  * MM_F32 context: MM_TC_TF32 or MM_TC_BF16 = the y passes of length 512 or
  * 1024 run their 32-point level on tensor cores with split operands (the
- * other passes stay FP32).
+ * other passes stay FP32): TF32 in hi + lo parts (about 21 bits), BF16 in
+ * hi + mid + lo parts with the six products down to 2^-23 (about 24 bits,
+ * within the FP32 tolerance).
  * MM_F64 context: MM_FFT_FF = all five passes in float-float arithmetic
  * (pairs of FP32 values, about 48 significant bits, on the FP32 pipes), and,
  * for uniform Ms and A without DMI or STT, the LLG stage kernel as well
@@ -322,6 +324,13 @@ int mm_dft32_tc(const void* in, void* out, long nlines, int mode, int direction,
  * powers of two.  Setting it allocates float-float
  * copies of the Newell octant and twiddle tables (6 (Pz/2+1)(Py/2+1) Hs x 8
  * bytes plus the tables), kept until mm_destroy.
+ * MM_F32 context with ny = 512 and nz = 16: MM_FFT_F4 = the y forward pass,
+ * the z transform with the tensor product and the y inverse pass fused into
+ * one pass over kx planes, each held on chip by a cluster of four CTAs (the
+ * 3-pass thin-film variant: the spectrum crosses HBM once between the x
+ * passes instead of three times); setting it allocates a copy of the octant
+ * laid out per kx plane (Hx x 4 x 6 x (Pz/2+1) x 256 floats) and a twiddle
+ * table, kept until mm_destroy.
  * Errors: INVALID_ARG (unknown mode, mode not valid for the context's
  * precision or mesh), NOMEM/CUDA (allocation or setup). */
 int mm_set_fft_mode(mm_ctx* ctx, int mode);

@@ -28,7 +28,7 @@ MM_ERR_DT_UNDERFLOW = -4
 MM_ERR_NOT_CONVERGED = -5
 MM_ERR_TIMEOUT = -6
 MM_ERR_NOMEM = -7
-MM_TC_TF32, MM_TC_BF16, MM_FFT_FF = 1, 2, 3
+MM_TC_TF32, MM_TC_BF16, MM_FFT_FF, MM_FFT_F4 = 1, 2, 3, 4
 MM_ROOF_FP64, MM_ROOF_FP32, MM_ROOF_FP32X2 = 0, 1, 2
 # kernel classes for mm_kernel_time
 MM_K_XFWD, MM_K_YFWD, MM_K_ZCONV, MM_K_YINV, MM_K_XINV, MM_K_STAGE, MM_K_CONTROL, MM_K_REDUCE = range(8)

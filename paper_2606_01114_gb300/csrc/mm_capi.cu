@@ -90,7 +90,7 @@ size_t elem(const mm_ctx* ctx) { return ctx->prec == MM_F64 ? sizeof(double) : s
 void free_all(mm_ctx* ctx) {
     void* ptrs[] = {ctx->Ms_cell, ctx->A_cell, ctx->kern, ctx->bufA, ctx->bufB, ctx->Hd, ctx->Hs_field,
                     ctx->m0, ctx->ms[0], ctx->ms[1], ctx->mnext, ctx->kptrs, ctx->ctl, ctx->tw.f64, ctx->tw.f32,
-                    ctx->tw.ff, ctx->kern_ff, ctx->adj, ctx->m_stage};
+                    ctx->tw.ff, ctx->kern_ff, ctx->adj, ctx->m_stage, ctx->kern_f4, ctx->tw_f4};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (void* p : ctx->k)

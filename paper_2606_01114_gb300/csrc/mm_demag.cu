@@ -498,23 +498,14 @@ __global__ void __launch_bounds__(3 * kZB)
     }
 }
 
-// K6 for the packed complex length L = L1 x L2 (64 <= L <= 512, L1 >= L2):
-// four-step transform of B rows through shared memory, with the
-// complex-to-real packing as a further shared-memory pass before it (a
-// variant that formed the packed values in the level-1 loads instead, with
-// compile-time twiddles and no first round trip, ran 2 % slower).
+// K6 for the packed complex length L = L1 x L2 (64 <= L <= 256, L1 >= L2;
+// L = 512 takes k_xinv_pk): four-step transform of B rows through shared
+// memory, with the complex-to-real packing as a further shared-memory pass
+// before it.
 // Level-1 threads (t < L2) hold z[t + L2 n1]; level-2 threads (k1 < L1)
 // hold row k1 of the L1 x L2 transpose, XOR-swizzled (xsw, shared with K2).
 template <int L1, int L2> __device__ __forceinline__ int xsw(int k1, int n2) {
     return k1 * L2 + (n2 ^ (k1 & (L2 - 1) & 15));
-}
-
-// f(std::integral_constant<int, I>) for I = I0 .. N-1, unrolled at compile time
-template <int I, int N, typename F> __device__ __forceinline__ void static_for(F&& f) {
-    if constexpr (I < N) {
-        f(std::integral_constant<int, I>{});
-        static_for<I + 1, N>(f);
-    }
 }
 
 template <int L1, int L2>
@@ -593,6 +584,71 @@ __global__ void __launch_bounds__(128, (L1 * L2 >= 512) ? 6 : 8)
 // w = exp(-2 pi i / Px), splits into a per-thread w^k1 (one table read) and
 // a compile-time w^(L1 k2).  Each output row is written straight from
 // registers: no shared-memory round trip and no barrier after level 2.
+// K6 for L = 512 as 16 x 32: level 1 with L2 = 32 threads per row (all 128
+// threads of the block) forms the packed values in its loads (X[n] and
+// X[L - n] straight from the spectrum, the twiddle exp(+2 pi i n / Px) as a
+// per-thread part times a compile-time part), so the packing needs no
+// shared-memory pass; one shared-memory transpose; level 2 on B x L1
+// threads.  (The same packing with the 32 x 16 split, where only half the
+// threads load, was 2 % slower than k_xinv_reg.)
+template <int L1, int L2>
+__global__ void __launch_bounds__(128, 6)
+    k_xinv_pk(const float2* __restrict__ in, int Hs, float* __restrict__ out, long rows, float scale,
+              const float2* __restrict__ twL, const float2* __restrict__ twP) {
+    constexpr int L = L1 * L2, B = 4, NX = L;
+    static_assert(B * L2 == 128, "level 1 takes every thread");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* S = reinterpret_cast<float2*>(smem_raw);      // [B][L]
+    const int tid = threadIdx.x;
+    const long r0 = (long)blockIdx.x * B;
+    {
+        const int t = tid % L2, b1 = tid / L2;
+        const long r = r0 + b1;
+        const bool ok = r < rows;
+        const float2* irow = in + (ok ? r : 0) * Hs;
+        const float2 wt = cconj(twP[t]);
+        float2 v[L1];
+        static_for<0, L1>([&](auto N1) {
+            constexpr int n1 = decltype(N1)::value;
+            const int n = t + L2 * n1;
+            const float2 xk = ok ? irow[n] : make_float2(0.f, 0.f);
+            const float2 xc = ok ? irow[L - n] : make_float2(0.f, 0.f);
+            const float2 c = cconj(xc);
+            const float2 e = cscale(cadd(xk, c), 0.5f);
+            float2 o = cmul(cscale(csub(xk, c), 0.5f), wt);
+            if constexpr (n1 > 0) {
+                constexpr double cc = cos2pi(n1, 2 * L1), ss = sin2pi(n1, 2 * L1);
+                o = cmul(o, make_float2((float)cc, (float)ss));
+            }
+            v[n1] = make_float2(e.x - o.y, e.y + o.x);
+        });
+        dif<L1, +1, false>(v);
+#pragma unroll
+        for (int k1 = 0; k1 < L1; ++k1) {
+            float2 y = v[dif_pos<L1>(k1)];
+            if (k1 > 0) y = cmul(y, cconj(twL[t * k1]));
+            S[b1 * L + xsw<L1, L2>(k1, t)] = y;
+        }
+    }
+    __syncthreads();
+    if (tid < B * L1) {
+        const int k1 = tid % L1, b2 = tid / L1;
+        const long r = r0 + b2;
+        float2 u[L2];
+#pragma unroll
+        for (int n2 = 0; n2 < L2; ++n2) u[n2] = S[b2 * L + xsw<L1, L2>(k1, n2)];
+        dif<L2, +1, false>(u);
+        if (r < rows) {
+            float2* op = reinterpret_cast<float2*>(out + r * NX);
+#pragma unroll
+            for (int k2 = 0; k2 < L2 / 2; ++k2) {
+                const float2 z = u[dif_pos<L2>(k2)];
+                op[k1 + L1 * k2] = make_float2(z.x * scale, z.y * scale);
+            }
+        }
+    }
+}
+
 template <int L1, int L2>
 __global__ void __launch_bounds__(128, 7)
     k_xfwd_reg(const float* __restrict__ in, const float* __restrict__ Ms, float ms, long ms_rows,
@@ -814,6 +870,15 @@ int launch_xinv_reg(mm_ctx* ctx, const float2* in, float* out, long rows, float 
                     const float2* twP) {
     constexpr int B = 4;
     const size_t smem = (size_t)B * L1 * L2 * sizeof(float2);
+    if constexpr (L1 * L2 == 512) {
+        // 16 x 32 with the packing folded into the level-1 loads: 53.3 -> 35.5 us on the 512 x 512 x 16 film
+        int rc = set_smem(ctx, (const void*)k_xinv_pk<16, 32>, smem);
+        if (rc) return rc;
+        k_xinv_pk<16, 32><<<(unsigned)((rows + B - 1) / B), 128, smem, ctx->stream>>>(in, ctx->Hs, out, rows, scale,
+                                                                                     twL, twP);
+        MM_LAUNCH_CHECK(ctx);
+        return MM_OK;
+    }
     int rc = set_smem(ctx, (const void*)k_xinv_reg<L1, L2>, smem);
     if (rc) return rc;
     k_xinv_reg<L1, L2><<<(unsigned)((rows + B - 1) / B), B * L1, smem, ctx->stream>>>(in, ctx->Hs, out, rows, scale,
@@ -978,6 +1043,11 @@ int apply(mm_ctx* ctx, const T* m, T* H, bool unit = false) {
                      table<T>(ctx, ctx->tw.off_lx), table<T>(ctx, ctx->tw.off_px), ctx->Px);
     if (rc) return rc;
     (void)plane;
+    if (sizeof(T) == 4 && ctx->fft_mode == MM_FFT_F4) {
+        // K3-K5 fused over kx planes, in place on the x pass's spectrum
+        if ((rc = f4_yzy(ctx, A))) return rc;
+        return xinv_pass<T>(ctx, A, H, rows);
+    }
     // K3
     if (ctx->Py > 1) {
         ColGeom g{ctx->Hs, ctx->Hs, 3 * ctx->nz, (long)ctx->ny * ctx->Hs, 0, (long)ctx->Py * ctx->Hs, 0};

@@ -97,6 +97,8 @@ struct mm_ctx {
     // buffers (path precision T; complex = 2T)
     void* kern;               // [6][Pz2][Py2][Hs] real k-space Newell octant
     void* kern_ff;            // float-float copy of kern (MM_FFT_FF), or NULL
+    void* kern_f4;            // octant re-laid out per kx plane for MM_FFT_F4, or NULL
+    void* tw_f4;              // twiddles of the fused MM_FFT_F4 pass, or NULL
     void* bufA;               // complex [3][nz][ny][Hs]
     void* bufB;               // complex [3][nz][Py][Hs]
     void* Hd;                 // [3][N] demag field of the current stage state
@@ -188,6 +190,11 @@ int demag_apply_unit(mm_ctx* ctx, const void* g, void* H);  // same with Ms = 1 
 int demag_prepare_ff(mm_ctx* ctx);                     // float-float tables for MM_FFT_FF
 // the tensor product of K4 on an unpruned R2C spectrum [3][Pz][Py][Hx] (in place)
 int demag_kspace_product(mm_ctx* ctx, void* spec);
+// MM_FFT_F4 (mm_f4.cu): the y forward, z product and y inverse passes fused
+// over kx planes in clusters of four CTAs (FP32, ny = 512, nz = 16)
+bool f4_supported(const mm_ctx* ctx);
+int f4_prepare(mm_ctx* ctx);
+int f4_yzy(mm_ctx* ctx, void* A);
 // surrogate network: its grid, and the stream its launches go to (returns the old one)
 void fno_grid(const mm_fno* f, int* nx, int* ny);
 cudaStream_t fno_swap_stream(mm_fno* f, cudaStream_t s);

@@ -723,7 +723,9 @@ __global__ void k_bb_grad(Params<T> p, const T* __restrict__ m, const T* __restr
     if (have_prev) {
         const double a0 = block_reduce_t<T>(ss, false);
         if (threadIdx.x == 0) atomicAdd(&ctl->bb[0], a0);
-        const double a1 = block_reduce_t<T>(sy, false);
+        // s.y is a difference-like sum (the BB quotients divide by it and
+        // read its sign), so its warp stage runs in double even in FP32
+        const double a1 = block_reduce_t<double>((double)sy, false);
         if (threadIdx.x == 0) atomicAdd(&ctl->bb[1], a1);
         const double a2 = block_reduce_t<T>(yy, false);
         if (threadIdx.x == 0) atomicAdd(&ctl->bb[2], a2);

@@ -52,6 +52,15 @@ constexpr double cos2pi(int k, int n) {
     return taylor_cos(2.0 * kPiTaylor * k / n);
 }
 
+// f(std::integral_constant<int, I>) for I = I0 .. N-1, unrolled at compile
+// time (so twiddles indexed by I fold to constants)
+template <int I, int N, typename F> __host__ __device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (I < N) {
+        f(std::integral_constant<int, I>{});
+        static_for<I + 1, N>(f);
+    }
+}
+
 // position of X[k] after dif<N>
 template <int N> __host__ __device__ constexpr int dif_pos(int k) {
     if constexpr (N <= 8) {

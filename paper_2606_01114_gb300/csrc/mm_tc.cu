@@ -37,6 +37,8 @@ __device__ __nv_bfloat16 g_dft_bf16[2][2][kTcN * kTcK];
 // then lo), copied into a block with 16-byte loads
 __device__ __align__(16) unsigned char g_bimg_tf32[2][2 * kTcN * kTcK * 4];
 __device__ __align__(16) unsigned char g_bimg_bf16[2][2 * kTcN * kTcK * 2];
+// BF16 in three parts (hi, mid, lo) for the y passes: about 24 bits
+__device__ __align__(16) unsigned char g_bimg_bf16x3[2][3 * kTcN * kTcK * 2];
 __device__ int g_tc_status;
 
 bool g_tables_ready[64] = {false};
@@ -79,6 +81,20 @@ __global__ void k_init_dft_images() {
         *reinterpret_cast<float*>(&g_bimg_tf32[d][kTcN * kTcK * 4 + o4]) = g_dft_f32[d][1][e];
         *reinterpret_cast<__nv_bfloat16*>(&g_bimg_bf16[d][o2]) = g_dft_bf16[d][0][e];
         *reinterpret_cast<__nv_bfloat16*>(&g_bimg_bf16[d][kTcN * kTcK * 2 + o2]) = g_dft_bf16[d][1][e];
+        {
+            const int j = e / kTcK, kk = e % kTcK;
+            const int k = j >> 1, n = kk >> 1;
+            double sn, cs;
+            sincospi((d == 0 ? -1.0 : 1.0) * 2.0 * (double)((n * k) % 32) / 32.0, &sn, &cs);
+            const double v = (j & 1) == 0 ? ((kk & 1) == 0 ? cs : -sn) : ((kk & 1) == 0 ? sn : cs);
+            const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+            const double r1 = v - (double)__bfloat162float(h);
+            const __nv_bfloat16 mid = __float2bfloat16_rn((float)r1);
+            const __nv_bfloat16 lo = __float2bfloat16_rn((float)(r1 - (double)__bfloat162float(mid)));
+            *reinterpret_cast<__nv_bfloat16*>(&g_bimg_bf16x3[d][o2]) = h;
+            *reinterpret_cast<__nv_bfloat16*>(&g_bimg_bf16x3[d][kTcN * kTcK * 2 + o2]) = mid;
+            *reinterpret_cast<__nv_bfloat16*>(&g_bimg_bf16x3[d][2 * kTcN * kTcK * 2 + o2]) = lo;
+        }
     }
 }
 
@@ -147,10 +163,10 @@ __global__ void k_wait_selftest(long limit, int* gave_up) {
 
 // Shared memory of one tile: A hi/lo [128 x 64], B hi/lo [64 x 64] (element
 // size ES), the mbarrier and the tensor-memory address.
-template <int ES> struct TcSmem {
+template <int ES, int PARTS = 2> struct TcSmem {
     static constexpr int A_BYTES = kTcLines * kTcK * ES;
     static constexpr int B_BYTES = kTcN * kTcK * ES;
-    static constexpr int BYTES = 2 * A_BYTES + 2 * B_BYTES + 64;
+    static constexpr int BYTES = PARTS * A_BYTES + PARTS * B_BYTES + 64;
 };
 
 // Batched 32-point DFT of `nlines` contiguous lines of 32 float2 values.
@@ -275,27 +291,33 @@ __global__ void __launch_bounds__(kTcLines) k_dft32_tc(const float2* __restrict_
 // transposed through shared memory; level 2 (thread (k1, b), L2-point DFT
 // over n2 in registers) writes X[k1 + 32 k2].  The DFT-matrix operand and
 // the tensor memory are set up once per block; the line operands are split
-// into hi + lo and stored 16 bytes at a time.  PIN: the upper half of the
-// input rows is zero (K = 32 real inputs); POUT: only the lower half of the
-// output rows is written.
+// into parts of the tensor-core type and stored 16 bytes at a time: TF32 hi +
+// lo (products hi.hi + hi.lo + lo.hi, about 21 bits), BF16 hi + mid + lo
+// (products hi.hi + hi.mid + mid.hi + mid.mid + hi.lo + lo.hi; the dropped
+// ones are below 2^-23 relative, so about 24 bits, the FP32 path's own
+// precision).  PIN: the upper half of the input rows is zero (K = 32 real
+// inputs); POUT: only the lower half of the output rows is written.
 template <int L2, int DIR, bool PIN, bool POUT, bool TF32>
 __global__ void __launch_bounds__(32 * (128 / L2))
     k_cols_tc(const float2* in, float2* out, int Hx, ColGeom cg, const float2* __restrict__ tw, int ntx,
               long ntiles) {
     constexpr int B = 128 / L2, L = 32 * L2;
     constexpr int ES = TF32 ? 4 : 2;
+    constexpr int PARTS = TF32 ? 2 : 3;
     constexpr int KA = PIN ? 32 : 64;
     constexpr int EPV = 16 / ES;                            // elements per 16-byte store
-    using S = TcSmem<ES>;
+    using S = TcSmem<ES, PARTS>;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* a_hi = smem;
     unsigned char* a_lo = smem + S::A_BYTES;
-    unsigned char* b_hi = smem + 2 * S::A_BYTES;
-    unsigned char* b_lo = b_hi + S::B_BYTES;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(b_lo + S::B_BYTES);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(b_lo + S::B_BYTES + 16);
+    unsigned char* a_mid = smem + 2 * S::A_BYTES;           // BF16 only
+    unsigned char* b_hi = smem + PARTS * S::A_BYTES;
+    unsigned char* b_part[3] = {b_hi, b_hi + S::B_BYTES, b_hi + 2 * S::B_BYTES};   // BF16: hi, mid, lo
+    unsigned char* b_lo = TF32 ? b_part[1] : b_part[2];
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(b_hi + PARTS * S::B_BYTES);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(b_hi + PARTS * S::B_BYTES + 16);
     float2* T = reinterpret_cast<float2*>(smem);            // level-2 transpose, reuses A after the MMA
-    static_assert(L * B * 8 <= 2 * S::A_BYTES, "transpose must fit in the A operand space");
+    static_assert(L * B * 8 <= PARTS * S::A_BYTES, "transpose must fit in the A operand space");
     const int tid = threadIdx.x, warp = tid >> 5;
     const int m = B < 16 ? 16 / B - 1 : 0;
     const uint32_t mbar_a = (uint32_t)__cvta_generic_to_shared(mbar);
@@ -309,10 +331,10 @@ __global__ void __launch_bounds__(32 * (128 / L2))
     }
     if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_a));
     {
-        // B (hi then lo): one image copy
-        const uint4* src = reinterpret_cast<const uint4*>(TF32 ? g_bimg_tf32[dir_index] : g_bimg_bf16[dir_index]);
+        // B (TF32: hi, lo; BF16: hi, mid, lo): one image copy
+        const uint4* src = reinterpret_cast<const uint4*>(TF32 ? g_bimg_tf32[dir_index] : g_bimg_bf16x3[dir_index]);
         uint4* dst = reinterpret_cast<uint4*>(b_hi);
-        for (int e = tid; e < 2 * S::B_BYTES / 16; e += blockDim.x) dst[e] = src[e];
+        for (int e = tid; e < PARTS * S::B_BYTES / 16; e += blockDim.x) dst[e] = src[e];
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -354,19 +376,27 @@ __global__ void __launch_bounds__(32 * (128 / L2))
                     *reinterpret_cast<float4*>(a_hi + o) = make_float4(h[0], h[1], h[2], h[3]);
                     *reinterpret_cast<float4*>(a_lo + o) = make_float4(l[0], l[1], l[2], l[3]);
                 } else {
-                    uint32_t hw[4], lw[4];   // element q at byte 2 q of the 16-byte slot
+                    uint32_t hw[4], mw[4], lw[4];   // element q at byte 2 q of the 16-byte slot
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const __nv_bfloat16 h0 = __float2bfloat16_rn(xs[2 * q]);
-                        const __nv_bfloat16 h1 = __float2bfloat16_rn(xs[2 * q + 1]);
-                        const __nv_bfloat162 hp = __halves2bfloat162(h0, h1);
-                        const __nv_bfloat162 lp = __halves2bfloat162(
-                            __float2bfloat16_rn(xs[2 * q] - __bfloat162float(h0)),
-                            __float2bfloat16_rn(xs[2 * q + 1] - __bfloat162float(h1)));
+                        __nv_bfloat16 hh[2], mm[2], ll[2];
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            const float x = xs[2 * q + u];
+                            hh[u] = __float2bfloat16_rn(x);
+                            const float r1 = x - __bfloat162float(hh[u]);      // exact
+                            mm[u] = __float2bfloat16_rn(r1);
+                            ll[u] = __float2bfloat16_rn(r1 - __bfloat162float(mm[u]));
+                        }
+                        const __nv_bfloat162 hp = __halves2bfloat162(hh[0], hh[1]);
+                        const __nv_bfloat162 mp = __halves2bfloat162(mm[0], mm[1]);
+                        const __nv_bfloat162 lp = __halves2bfloat162(ll[0], ll[1]);
                         hw[q] = *reinterpret_cast<const uint32_t*>(&hp);
+                        mw[q] = *reinterpret_cast<const uint32_t*>(&mp);
                         lw[q] = *reinterpret_cast<const uint32_t*>(&lp);
                     }
                     *reinterpret_cast<uint4*>(a_hi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    *reinterpret_cast<uint4*>(a_mid + o) = make_uint4(mw[0], mw[1], mw[2], mw[3]);
                     *reinterpret_cast<uint4*>(a_lo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                 }
             }
@@ -378,12 +408,17 @@ __global__ void __launch_bounds__(32 * (128 / L2))
         if (tid == 0) {
             const uint32_t idesc = instr_desc<TF32>();
             const uint32_t sbo = (kTcK / (16 / ES)) * 128;
-            const uint32_t A[2] = {(uint32_t)__cvta_generic_to_shared(a_hi), (uint32_t)__cvta_generic_to_shared(a_lo)};
-            const uint32_t Bm[2] = {(uint32_t)__cvta_generic_to_shared(b_hi), (uint32_t)__cvta_generic_to_shared(b_lo)};
-            const int pa[3] = {0, 0, 1}, pb[3] = {0, 1, 0};
+            // parts: 0 hi, 1 lo, 2 mid (BF16)
+            const uint32_t A[3] = {(uint32_t)__cvta_generic_to_shared(a_hi), (uint32_t)__cvta_generic_to_shared(a_lo),
+                                   (uint32_t)__cvta_generic_to_shared(a_mid)};
+            const uint32_t Bm[3] = {(uint32_t)__cvta_generic_to_shared(b_hi), (uint32_t)__cvta_generic_to_shared(b_lo),
+                                    (uint32_t)__cvta_generic_to_shared(b_part[1])};
+            // TF32: hi.hi, hi.lo, lo.hi; BF16 adds hi.mid, mid.hi, mid.mid
+            constexpr int NPROD = TF32 ? 3 : 6;
+            const int pa[6] = {0, 0, 1, 0, 2, 2}, pb[6] = {0, 1, 0, 2, 0, 2};
             constexpr int KMMA = TF32 ? 8 : 16;
             uint32_t acc = 0;
-            for (int q = 0; q < 3; ++q)
+            for (int q = 0; q < NPROD; ++q)
                 for (int kc = 0; kc < KA / KMMA; ++kc) {
                     mma<TF32>(tmem, smem_desc(A[pa[q]] + kc * 256, 128, sbo), smem_desc(Bm[pb[q]] + kc * 256, 128, sbo),
                               idesc, acc);
@@ -458,7 +493,7 @@ __global__ void __launch_bounds__(32 * (128 / L2))
 template <int L2, int DIR, bool TF32>
 int launch_cols_tc(mm_ctx* ctx, const float2* in, float2* out, int nplanes, ColGeom g, const float2* tw) {
     constexpr int B = 128 / L2;
-    const int bytes = TcSmem<TF32 ? 4 : 2>::BYTES;
+    const int bytes = TF32 ? TcSmem<4, 2>::BYTES : TcSmem<2, 3>::BYTES;
     auto fn = k_cols_tc<L2, DIR, (DIR < 0), (DIR > 0), TF32>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return fail(ctx, MM_ERR_CUDA, "tensor-core pass setup: %s", cudaGetErrorString(e));
@@ -515,8 +550,17 @@ using namespace mm;
 
 extern "C" int mm_set_fft_mode(mm_ctx* ctx, int mode) {
     if (!ctx) return fail(nullptr, MM_ERR_INVALID_ARG, "ctx is NULL");
-    if (mode != 0 && mode != MM_TC_TF32 && mode != MM_TC_BF16 && mode != MM_FFT_FF)
+    if (mode != 0 && mode != MM_TC_TF32 && mode != MM_TC_BF16 && mode != MM_FFT_FF && mode != MM_FFT_F4)
         return fail(ctx, MM_ERR_INVALID_ARG, "bad FFT mode %d", mode);
+    if (mode == MM_FFT_F4) {
+        if (!f4_supported(ctx))
+            return fail(ctx, MM_ERR_INVALID_ARG, "the fused y-z-y pass needs an MM_F32 context with ny = 512, nz = 16");
+        MM_BIND(ctx);
+        int rc = f4_prepare(ctx);
+        if (rc) return rc;
+        ctx->fft_mode = mode;
+        return MM_OK;
+    }
     if (mode == MM_FFT_FF) {
         auto p2 = [](int n) { return n > 0 && (n & (n - 1)) == 0; };
         if (ctx->prec != MM_F64) return fail(ctx, MM_ERR_INVALID_ARG, "float-float passes need an MM_F64 context");

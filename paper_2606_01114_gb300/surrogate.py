@@ -113,9 +113,10 @@ def per_eval_ms(fn, reps=200):
     return a.elapsed_time(b) / reps
 
 
-def gain(ctx, f, film, seeds, t_max, torque_tol, k_exact, bound, torque_exact):
+def gain(ctx, f, film, seeds, t_max, torque_tol, k_exact, bound, torque_exact, log=None):
     """Relax each seeded state with the plain solver and with the surrogate;
-    device-synchronised wall time and relaxed energies per state."""
+    device-synchronised wall time and relaxed energies per state (each row
+    is also printed as it completes, when `log` is given)."""
     rows = []
     for seed in seeds:
         m0 = initial_state(film, seed)
@@ -136,10 +137,15 @@ def gain(ctx, f, film, seeds, t_max, torque_tol, k_exact, bound, torque_exact):
             E = mm_energy(ctx, m)
             row[mode] = {"seconds": wall, "t": t, "steps": steps, "energy": float(np.sum(E)),
                          "torque": mm_max_torque(ctx, m), **(stats or {})}
-        m = m0.clone()
-        row["plain_steps_to_torque_exact"] = mm_relax(ctx, m, t_max, max(torque_exact, torque_tol))[1]
+        if torque_exact > torque_tol:
+            m = m0.clone()
+            row["plain_steps_to_torque_exact"] = mm_relax(ctx, m, t_max, torque_exact)[1]
+        else:
+            row["plain_steps_to_torque_exact"] = row["plain"]["steps"]
         row["energy_rel_err"] = abs(row["surrogate"]["energy"] - row["plain"]["energy"]) / abs(row["plain"]["energy"])
         rows.append(row)
+        if log:
+            print(json.dumps(row), file=log, flush=True)
     return rows
 
 
@@ -185,6 +191,10 @@ def main(argv=None):
     ap.add_argument("--bound", type=float, default=1e-3)
     ap.add_argument("--torque-exact", type=float, default=1e-2)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--params-out", default=None, help="save the trained parameters (numpy .npy) here")
+    ap.add_argument("--params-in", default=None,
+                    help="load trained parameters from this .npy and skip data generation and training")
+    ap.add_argument("--rows-log", default=None, help="append each test state's result (JSON line) as it completes")
     ap.add_argument("--timing", action="store_true", help="time the network's kernels only and exit")
     a = ap.parse_args(argv)
     film = FILM
@@ -195,26 +205,35 @@ def main(argv=None):
     ctx = film_context(film)
     res = {"film": {k: list(v) if isinstance(v, tuple) else v for k, v in film.items()}, "args": vars(a)}
 
-    t0 = time.perf_counter()
-    ms, hs = generate_pairs(ctx, film, a.trajectories, a.per_trajectory, seed0=100)
-    torch.cuda.synchronize()
-    res["pairs"] = int(ms.shape[0])
-    res["generate_seconds"] = time.perf_counter() - t0
-    print(f"{ms.shape[0]} pairs in {res['generate_seconds']:.1f} s", flush=True)
     vm, vh = generate_pairs(ctx, film, 8, 8, seed0=20000)
-
     f = mm_fno_create(film["n"][0], film["n"][1], width=a.width, modes=a.modes, layers=a.layers,
                       store_bf16=not a.fp32_storage, max_batch=max(a.batch, 16), seed=7)
-    t0 = time.perf_counter()
-    losses = train(f, ms, hs, a.train_steps, a.batch, a.lr, log_every=max(a.train_steps // 20, 1))
-    torch.cuda.synchronize()
-    res["train_seconds"] = time.perf_counter() - t0
-    res["train_loss_first"] = float(np.mean(losses[:10]))
-    res["train_loss_last"] = float(np.mean(losses[-50:]))
+    if a.params_in:
+        mm_fno_params(f, set_params=np.load(a.params_in).astype(np.float32))
+        res["params_in"] = a.params_in
+    else:
+        t0 = time.perf_counter()
+        ms, hs = generate_pairs(ctx, film, a.trajectories, a.per_trajectory, seed0=100)
+        torch.cuda.synchronize()
+        res["pairs"] = int(ms.shape[0])
+        res["generate_seconds"] = time.perf_counter() - t0
+        print(f"{ms.shape[0]} pairs in {res['generate_seconds']:.1f} s", flush=True)
+        t0 = time.perf_counter()
+        losses = train(f, ms, hs, a.train_steps, a.batch, a.lr, log_every=max(a.train_steps // 20, 1))
+        torch.cuda.synchronize()
+        res["train_seconds"] = time.perf_counter() - t0
+        res["train_loss_first"] = float(np.mean(losses[:10]))
+        res["train_loss_last"] = float(np.mean(losses[-50:]))
+        del ms, hs
+        if a.params_out:
+            np.save(a.params_out, mm_fno_params(f)[0])
     res["val_rel_l2_mean"], res["val_rel_l2_max"] = evaluate(f, vm, vh, 16)
-    print(f"trained in {res['train_seconds']:.1f} s; validation rel-L2 mean {res['val_rel_l2_mean']:.3e} "
-          f"max {res['val_rel_l2_max']:.3e}", flush=True)
-    del ms, hs
+    print(f"validation rel-L2 mean {res['val_rel_l2_mean']:.3e} max {res['val_rel_l2_max']:.3e}", flush=True)
+    if a.test_states == 0:
+        if a.out:
+            with open(a.out, "w") as fh:
+                json.dump(res, fh, indent=1)
+        return res
 
     m1 = initial_state(film, 30000)
     H1 = torch.empty_like(m1)
@@ -224,8 +243,11 @@ def main(argv=None):
     print(f"per evaluation: exact demag {res['exact_demag_ms']:.4f} ms, surrogate {res['surrogate_eval_ms']:.4f} ms",
           flush=True)
 
+    log = open(a.rows_log, "a") if a.rows_log else None
     rows = gain(ctx, f, film, range(10000, 10000 + a.test_states), a.t_max, a.torque_tol, a.k_exact, a.bound,
-                a.torque_exact)
+                a.torque_exact, log=log)
+    if log:
+        log.close()
     tp = sum(r["plain"]["seconds"] for r in rows)
     ts = sum(r["surrogate"]["seconds"] for r in rows)
     errs = np.array([r["energy_rel_err"] for r in rows])

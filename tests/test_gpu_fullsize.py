@@ -35,6 +35,7 @@ MODES = {
     "f32": (mm.MM_F32, 0, 1e-5),
     "f64": (mm.MM_F64, 0, 1e-12),
     "ff": (mm.MM_F64, mm.MM_FFT_FF, 1e-12),
+    "f4": (mm.MM_F32, mm.MM_FFT_F4, 1e-5),      # the fused y-z-y pass over kx planes
 }
 RKF45_STEPS = 4
 
@@ -162,3 +163,29 @@ def test_film512_rkf45_first_steps_match_oracle_trajectory(mode):
               f"err {err:.3e} (oracle {err_ref:.3e}), state rel-L2 {rel:.2e}")
         t, dt = t_new, dt_next
     mm.mm_destroy(ctx)
+
+
+@pytest.mark.parametrize("n", [(16, 512, 16), (40, 512, 16)])
+def test_fused_yzy_pass_on_narrow_films_matches_oracle(n):
+    """MM_FFT_F4 on meshes of the supported ny and nz with few x cells (a
+    power of two and a direct-DFT x length): demag against the oracle,
+    element by element."""
+    d = (2e-9, 2e-9, 2e-9)
+    p = micromag.Problem(n, d)
+    m = wl.random_unit(n, seed=12)
+    ctx = mm.mm_init_mesh(*n, *d, precision=mm.MM_F32)
+    mm.mm_set_fft_mode(ctx, mm.MM_FFT_F4)
+    md = torch.tensor(m, dtype=torch.float32, device="cuda")
+    H = torch.empty_like(md)
+    mm.mm_demag_field(ctx, md, H)
+    check_elementwise(host(H), p.demag_fft(m), 1e-5, "demag")
+    mm.mm_destroy(ctx)
+
+
+def test_fused_yzy_pass_rejects_other_meshes():
+    for n, prec in (((64, 256, 16), mm.MM_F32), ((64, 512, 8), mm.MM_F32), ((64, 512, 16), mm.MM_F64)):
+        ctx = mm.mm_init_mesh(*n, 2e-9, 2e-9, 2e-9, precision=prec)
+        with pytest.raises(mm.MMError) as e:
+            mm.mm_set_fft_mode(ctx, mm.MM_FFT_F4)
+        assert e.value.code == mm.MM_ERR_INVALID_ARG
+        mm.mm_destroy(ctx)
