@@ -29,7 +29,9 @@
  *     Calls that return host scalars (energies, torque, step errors) wait for
  *     that stream.  Calls on one context must not overlap on the host.
  *   - Mesh sizes: nx, ny any of 1..512 (powers of two take the radix-2 passes,
- *     other sizes a direct O(n^2)-per-line DFT); nz 1 or a power of two up to 512.
+ *     other sizes Bluestein chirp-z passes of the next power of two >= 2P - 1,
+ *     or a direct DFT when the padded length P is at most 64); nz 1 or a power
+ *     of two up to 512.
  *   - Every function returns MM_OK (0) or a negative MM_ERR_* code;
  *     mm_last_error() then describes the failure.  A failed call leaves the
  *     caller's buffers in an unspecified state but the context usable, except

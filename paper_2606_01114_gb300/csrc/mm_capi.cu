@@ -90,7 +90,10 @@ size_t elem(const mm_ctx* ctx) { return ctx->prec == MM_F64 ? sizeof(double) : s
 void free_all(mm_ctx* ctx) {
     void* ptrs[] = {ctx->Ms_cell, ctx->A_cell, ctx->kern, ctx->bufA, ctx->bufB, ctx->Hd, ctx->Hs_field,
                     ctx->m0, ctx->ms[0], ctx->ms[1], ctx->mnext, ctx->kptrs, ctx->ctl, ctx->tw.f64, ctx->tw.f32,
-                    ctx->tw.ff, ctx->kern_ff, ctx->adj, ctx->m_stage, ctx->kern_f4, ctx->tw_f4};
+                    ctx->tw.ff, ctx->kern_ff, ctx->adj, ctx->m_stage, ctx->kern_f4, ctx->tw_f4,
+                    ctx->blue_x.chirp, ctx->blue_x.filt, ctx->blue_x.tw, ctx->blue_y.chirp, ctx->blue_y.filt,
+                    ctx->blue_y.tw, ctx->blue_x.chirp32, ctx->blue_x.filt32, ctx->blue_x.tw32, ctx->blue_y.chirp32,
+                    ctx->blue_y.filt32, ctx->blue_y.tw32};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (void* p : ctx->k)
@@ -295,6 +298,7 @@ int mm_init_mesh(mm_ctx** out, int nx, int ny, int nz, double dx, double dy, dou
         if (ce != cudaSuccess) rc = fail(ctx, MM_ERR_CUDA, "cudaMemcpy: %s", cudaGetErrorString(ce));
     }
     if (rc == MM_OK) rc = make_tables(ctx);
+    if (rc == MM_OK) rc = blue_prepare(ctx);
     if (rc == MM_OK) {
         reset_ctl(ctx->ctl_host, 0.0, 1e-14, std::numeric_limits<double>::infinity(), 1e-5);
         rc = push_ctl(ctx);

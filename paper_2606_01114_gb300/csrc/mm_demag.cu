@@ -321,6 +321,162 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512)
 // power-of-two passes, not a fast one.
 inline bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
+// Bluestein (chirp-z) passes for padded lengths P that are not powers of two
+// (meshes such as 100 x 25 or 350^3): with nk = (n^2 + k^2 - (k - n)^2) / 2,
+//   X[k] = sum_{n < nin} x[n] w^{nk} = a[k] sum_n (x[n] a[n]) b[k - n],
+// w = exp(DIR 2 pi i / P), a[n] = exp(DIR i pi n^2 / P), b = conj(a): a
+// linear convolution, done as a circular one of length M (the power of two
+// >= 2P - 1, so |k - n| < P never wraps) with the power-of-two Stockham
+// engine: chirp, FFT_M, times the filter spectrum (precomputed, scaled by
+// 1/M), inverse FFT_M, chirp.  O(M log M) per line instead of O(nin nout).
+template <typename T, int DIR>
+__device__ void blue_core(C_t<T>* s, const FftGeom& g, int nin, int nout, const C_t<T>* __restrict__ chirp,
+                          const C_t<T>* __restrict__ filt, const C_t<T>* __restrict__ twM) {
+    using C = C_t<T>;
+    const int M = g.L, B = g.NL;
+    for (int idx = threadIdx.x; idx < B * nin; idx += blockDim.x) {
+        const int b = idx % B, n = idx / B;
+        C a = chirp[n];
+        if (DIR > 0) a = cconj(a);
+        const int o = sidx(g, 0, n, b);
+        s[o] = cmul(s[o], a);
+    }
+    __syncthreads();
+    fft_lines<-1>(s, g, twM);
+    const C* V = filt + (DIR > 0 ? M : 0);
+    for (int idx = threadIdx.x; idx < B * M; idx += blockDim.x) {
+        const int b = idx % B, k = idx / B;
+        const int o = sidx(g, 0, k, b);
+        s[o] = cmul(s[o], V[k]);
+    }
+    __syncthreads();
+    fft_lines<+1>(s, g, twM);
+    for (int idx = threadIdx.x; idx < B * nout; idx += blockDim.x) {
+        const int b = idx % B, k = idx / B;
+        C a = chirp[k];
+        if (DIR > 0) a = cconj(a);
+        const int o = sidx(g, 0, k, b);
+        s[o] = cmul(s[o], a);
+    }
+    __syncthreads();
+}
+
+// K3 / K5: B adjacent columns of one plane per block
+template <typename T, int DIR>
+__global__ void k_cols_blue(const C_t<T>* __restrict__ in, C_t<T>* __restrict__ out, int nin, int nout, int Hx,
+                            int lgM, int lgB, ColGeom cg, const C_t<T>* __restrict__ chirp,
+                            const C_t<T>* __restrict__ filt, const C_t<T>* __restrict__ twM) {
+    using C = C_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* s = reinterpret_cast<C*>(smem_raw);
+    const int M = 1 << lgM, B = 1 << lgB;
+    const FftGeom g = fft_geom(M, B, 1, sizeof(C));
+    const int col0 = blockIdx.x << lgB;
+    const int p = blockIdx.y;
+    const int pi = p % cg.n_inner, po = p / cg.n_inner;
+    const C* ib = in + pi * cg.in_inner + po * cg.in_outer;
+    C* ob = out + pi * cg.out_inner + po * cg.out_outer;
+    for (int idx = threadIdx.x; idx < B * M; idx += blockDim.x) {
+        const int b = idx & (B - 1), n = idx >> lgB;
+        const int col = col0 + b;
+        s[sidx(g, 0, n, b)] = (n < nin && col < Hx) ? ib[(long)n * cg.rs_in + col] : cmk<C>(0, 0);
+    }
+    __syncthreads();
+    blue_core<T, DIR>(s, g, nin, nout, chirp, filt, twM);
+    for (int idx = threadIdx.x; idx < B * nout; idx += blockDim.x) {
+        const int b = idx & (B - 1), k = idx >> lgB;
+        const int col = col0 + b;
+        if (col < Hx) ob[(long)k * cg.rs_out + col] = s[sidx(g, 0, k, b)];
+    }
+}
+
+// K2: B rows per block, X_k for k < Hx of the real row (nin values, times Ms)
+template <typename T>
+__global__ void k_xfwd_blue(const T* __restrict__ in, long in_ld, int nin, const T* __restrict__ Ms, T ms,
+                            long ms_rows, C_t<T>* __restrict__ out, int Hs, int Hx, long rows, int lgM, int lgB,
+                            const C_t<T>* __restrict__ chirp, const C_t<T>* __restrict__ filt,
+                            const C_t<T>* __restrict__ twM) {
+    using C = C_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* s = reinterpret_cast<C*>(smem_raw);
+    const int M = 1 << lgM, B = 1 << lgB;
+    const FftGeom g = fft_geom(M, B, 1, sizeof(C));
+    const long r0 = (long)blockIdx.x << lgB;
+    for (int idx = threadIdx.x; idx < B * M; idx += blockDim.x) {
+        const int n = idx & (M - 1), b = idx >> lgM;
+        const long r = r0 + b;
+        T v = 0;
+        if (n < nin && r < rows) v = in[r * in_ld + n] * (Ms ? Ms[(r % ms_rows) * in_ld + n] : ms);
+        s[sidx(g, 0, n, b)] = cmk<C>(v, (T)0);
+    }
+    __syncthreads();
+    blue_core<T, -1>(s, g, nin, Hx, chirp, filt, twM);
+    for (int idx = threadIdx.x; idx < B * Hx; idx += blockDim.x) {
+        const int k = idx % Hx, b = idx / Hx;
+        const long r = r0 + b;
+        if (r < rows) out[r * Hs + k] = s[sidx(g, 0, k, b)];
+    }
+}
+
+// K6: B rows per block, out_x = scale / 2 [Re(sum_{k < nx} c_k X_k e^{+2 pi i k x / Px}) + (-1)^x Re X_nx],
+// c_0 = 1, c_k = 2 (the full inverse over Px of a Hermitian spectrum)
+template <typename T>
+__global__ void k_xinv_blue(const C_t<T>* __restrict__ in, int Hs, T* __restrict__ out, int nx, long rows, T scale,
+                            int lgM, int lgB, const C_t<T>* __restrict__ chirp, const C_t<T>* __restrict__ filt,
+                            const C_t<T>* __restrict__ twM) {
+    using C = C_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* s = reinterpret_cast<C*>(smem_raw);
+    const int M = 1 << lgM, B = 1 << lgB;
+    const FftGeom g = fft_geom(M, B, 1, sizeof(C));
+    const long r0 = (long)blockIdx.x << lgB;
+    for (int idx = threadIdx.x; idx < B * M; idx += blockDim.x) {
+        const int k = idx & (M - 1), b = idx >> lgM;
+        const long r = r0 + b;
+        C v = cmk<C>(0, 0);
+        if (k < nx && r < rows) {
+            v = in[r * Hs + k];
+            if (k > 0) v = cmk<C>(v.x + v.x, v.y + v.y);
+        }
+        s[sidx(g, 0, k, b)] = v;
+    }
+    __syncthreads();
+    blue_core<T, +1>(s, g, nx, nx, chirp, filt, twM);
+    const T half = (T)0.5 * scale;
+    for (int idx = threadIdx.x; idx < B * nx; idx += blockDim.x) {
+        const int x = idx % nx, b = idx / nx;
+        const long r = r0 + b;
+        if (r >= rows) continue;
+        const T ny_ = in[r * Hs + nx].x;
+        out[r * nx + x] = half * (s[sidx(g, 0, x, b)].x + ((x & 1) ? -ny_ : ny_));
+    }
+}
+
+// lines per Bluestein block: at most 1024 active threads (B M / 8) and 64 KB of shared memory
+inline int blue_lines(int M, int cs) {
+    int b = 1;
+    while (2 * b * M / 8 <= 1024 && (size_t)2 * b * M * cs <= 65536) b *= 2;
+    return b;
+}
+
+// the Bluestein arrays of an axis at precision T
+template <typename T> struct BlueArrays {
+    const C_t<T>* chirp;
+    const C_t<T>* filt;
+    const C_t<T>* tw;
+};
+template <typename T> BlueArrays<T> blue_arrays(const Blue& bl);
+template <> BlueArrays<double> blue_arrays<double>(const Blue& bl) {
+    return {(const double2*)bl.chirp, (const double2*)bl.filt, (const double2*)bl.tw};
+}
+template <> BlueArrays<float> blue_arrays<float>(const Blue& bl) {
+    return {(const float2*)bl.chirp32, (const float2*)bl.filt32, (const float2*)bl.tw32};
+}
+// float-float passes need power-of-two lengths (checked when the mode is set)
+template <> BlueArrays<ff> blue_arrays<ff>(const Blue&) { return {nullptr, nullptr, nullptr}; }
+// Bluestein takes over from the direct DFT above this length
+constexpr int kBlueMin = 64;
+
 // K2: X_k = sum_{x < nin} M_x exp(-2 pi i k x / Px), k = 0 .. Hx - 1
 template <typename T>
 __global__ void k_xfwd_direct(const T* __restrict__ in, long in_ld, int nin, const T* __restrict__ Ms, T ms,
@@ -575,15 +731,6 @@ __global__ void __launch_bounds__(128, (L1 * L2 >= 512) ? 6 : 8)
     }
 }
 
-// K2 for the packed complex length L = L1 x L2 (64 <= L <= 512, L1 >= L2):
-// four-step transform of B rows, level 1 through shared memory, with the
-// real-to-complex unpacking done in registers: after level 2,
-// thread (k1, b) holds Z[k1 + L1 k2] of its row, and the partner value
-// conj Z[L - k] comes from lane L1 - k1 of the same row by a warp shuffle
-// (lane 0 of the row pairs with itself, k2 <-> L2 - k2).  The twiddle w^k,
-// w = exp(-2 pi i / Px), splits into a per-thread w^k1 (one table read) and
-// a compile-time w^(L1 k2).  Each output row is written straight from
-// registers: no shared-memory round trip and no barrier after level 2.
 // K6 for L = 512 as 16 x 32: level 1 with L2 = 32 threads per row (all 128
 // threads of the block) forms the packed values in its loads (X[n] and
 // X[L - n] straight from the spectrum, the twiddle exp(+2 pi i n / Px) as a
@@ -649,7 +796,19 @@ __global__ void __launch_bounds__(128, 6)
     }
 }
 
-template <int L1, int L2>
+// K2 for the packed complex length L = L1 x L2 (64 <= L <= 512, L1 >= L2):
+// four-step transform of B rows, level 1 through shared memory, with the
+// real-to-complex unpacking done in registers: after level 2,
+// thread (k1, b) holds Z[k1 + L1 k2] of its row, and the partner value
+// conj Z[L - k] comes from lane L1 - k1 of the same row by a warp shuffle
+// (lane 0 of the row pairs with itself, k2 <-> L2 - k2).  The twiddle w^k,
+// w = exp(-2 pi i / Px), splits into a per-thread w^k1 (one table read) and
+// a compile-time w^(L1 k2).  Each output row is written straight from
+// registers: no shared-memory round trip and no barrier after level 2.
+// PQ (L = 512): level 1 runs on all 128 threads instead of B L2 = 64, each
+// thread taking one output parity of the L1-point transform (16 values
+// instead of 32), so no warp idles at the barrier.
+template <int L1, int L2, bool PQ = false>
 __global__ void __launch_bounds__(128, 7)
     k_xfwd_reg(const float* __restrict__ in, const float* __restrict__ Ms, float ms, long ms_rows,
                 float2* __restrict__ out, int Hs, long rows, const float2* __restrict__ twL,
@@ -660,7 +819,48 @@ __global__ void __launch_bounds__(128, 7)
     float2* S = reinterpret_cast<float2*>(smem_raw);      // [B][L]
     const int tid = threadIdx.x;
     const long r0 = (long)blockIdx.x * B;
-    if (tid < B * L2) {
+    if constexpr (PQ) {
+        // level 1 on every thread: the L1-point transform of L1/2 non-zero
+        // inputs split by output parity q (warps 0-1 even k1, 2-3 odd k1):
+        // X[2j] = DFT_{L1/2}(x)[j], X[2j + 1] = DFT_{L1/2}(x w^n)[j]
+        static_assert(2 * B * L2 == B * L1, "two parity classes fill the block");
+        constexpr int H = L1 / 2;
+        const int t = tid % L2, b = (tid / L2) % B, q = tid / (L2 * B);
+        const long r = r0 + b;
+        const bool act = r < rows;
+        const float2* rowp = reinterpret_cast<const float2*>(in + (act ? r : 0) * NX);
+        const float2* msp = Ms ? reinterpret_cast<const float2*>(Ms + ((act ? r : 0) % ms_rows) * NX) : nullptr;
+        float2 v[H];
+#pragma unroll
+        for (int n1 = 0; n1 < H; ++n1) {
+            const int j = t + L2 * n1;
+            float2 a = act ? rowp[j] : make_float2(0.f, 0.f);
+            if (msp) {
+                float2 w = msp[j];
+                a.x *= w.x;
+                a.y *= w.y;
+            } else {
+                a.x *= ms;
+                a.y *= ms;
+            }
+            v[n1] = a;
+        }
+        if (q) {
+            static_for<1, H>([&](auto N) {
+                constexpr int n = decltype(N)::value;
+                constexpr double c = cos2pi(n, L1), sn = -sin2pi(n, L1);
+                v[n] = cmul(v[n], make_float2((float)c, (float)sn));
+            });
+        }
+        dif<H, -1, false>(v);
+#pragma unroll
+        for (int jj = 0; jj < H; ++jj) {
+            const int k1 = 2 * jj + q;
+            float2 y = v[dif_pos<H>(jj)];
+            if (k1 > 0) y = cmul(y, twL[t * k1]);
+            S[b * L + xsw<L1, L2>(k1, t)] = y;
+        }
+    } else if (tid < B * L2) {
         const int t = tid % L2, b = tid / L2;
         const long r = r0 + b;
         const bool act = r < rows;
@@ -840,6 +1040,15 @@ int launch_xfwd_reg(mm_ctx* ctx, const float* in, const float* Ms, float ms, lon
                     const float2* twL, const float2* twP) {
     constexpr int B = 4;
     const size_t smem = (size_t)B * L1 * L2 * sizeof(float2);
+    if constexpr (L1 == 32 && L2 == 16) {
+        // level 1 split by output parity over all 128 threads: 39.0 -> 33.4 us on the 512 x 512 x 16 film
+        int rc = set_smem(ctx, (const void*)k_xfwd_reg<L1, L2, true>, smem);
+        if (rc) return rc;
+        k_xfwd_reg<L1, L2, true><<<(unsigned)((rows + B - 1) / B), B * L1, smem, ctx->stream>>>(
+            in, Ms, ms, ms_rows, out, ctx->Hs, rows, twL, twP);
+        MM_LAUNCH_CHECK(ctx);
+        return MM_OK;
+    }
     int rc = set_smem(ctx, (const void*)k_xfwd_reg<L1, L2>, smem);
     if (rc) return rc;
     k_xfwd_reg<L1, L2><<<(unsigned)((rows + B - 1) / B), B * L1, smem, ctx->stream>>>(in, Ms, ms, ms_rows, out,
@@ -903,6 +1112,18 @@ int try_xinv_reg(mm_ctx* ctx, const float2* in, float* out, long rows, float sca
 template <typename T>
 int run_xfwd(mm_ctx* ctx, const T* in, long in_ld, int nin, const T* Ms, T ms, long ms_rows, C_t<T>* out,
              long rows, const C_t<T>* twL, const C_t<T>* twP, int Px) {
+    if (!pow2(Px) && Px > kBlueMin && ctx->blue_x.P == Px) {
+        KernelTimer kt(ctx, MM_K_XFWD);
+        const BlueArrays<T> ba = blue_arrays<T>(ctx->blue_x);
+        const int M = ctx->blue_x.M, B = blue_lines(M, sizeof(C_t<T>));
+        const size_t smem = (size_t)B * M * sizeof(C_t<T>);
+        int rc = set_smem(ctx, (const void*)k_xfwd_blue<T>, smem);
+        if (rc) return rc;
+        k_xfwd_blue<T><<<(unsigned)((rows + B - 1) / B), block_threads(B * M / 8), smem, ctx->stream>>>(
+            in, in_ld, nin, Ms, ms, ms_rows, out, ctx->Hs, ctx->Hx, rows, ilog2(M), ilog2(B), ba.chirp, ba.filt, ba.tw);
+        MM_LAUNCH_CHECK(ctx);
+        return MM_OK;
+    }
     if (!pow2(Px)) {
         KernelTimer kt(ctx, MM_K_XFWD);
         const long n = rows * ctx->Hx;
@@ -970,6 +1191,19 @@ template <typename T, int DIR>
 int run_cols(mm_ctx* ctx, const C_t<T>* in, C_t<T>* out, int L, int nin, int nout, int nplanes, ColGeom g,
              const C_t<T>* tw) {
     KernelTimer kt(ctx, DIR < 0 ? MM_K_YFWD : MM_K_YINV);
+    if (!pow2(L) && L > kBlueMin && ctx->blue_y.P == L) {
+        if ((const void*)in == (const void*)out) return fail(ctx, MM_ERR_INVALID_ARG, "Bluestein pass needs out != in");
+        const BlueArrays<T> ba = blue_arrays<T>(ctx->blue_y);
+        const int M = ctx->blue_y.M, B = blue_lines(M, sizeof(C_t<T>));
+        const size_t smem = (size_t)B * M * sizeof(C_t<T>);
+        int rc = set_smem(ctx, (const void*)k_cols_blue<T, DIR>, smem);
+        if (rc) return rc;
+        dim3 grid((unsigned)((ctx->Hx + B - 1) / B), (unsigned)nplanes);
+        k_cols_blue<T, DIR><<<grid, block_threads(B * M / 8), smem, ctx->stream>>>(
+            in, out, nin, nout, ctx->Hx, ilog2(M), ilog2(B), g, ba.chirp, ba.filt, ba.tw);
+        MM_LAUNCH_CHECK(ctx);
+        return MM_OK;
+    }
     if (!pow2(L)) {
         if ((const void*)in == (const void*)out) return fail(ctx, MM_ERR_INVALID_ARG, "direct DFT pass needs out != in");
         dim3 grid((unsigned)(((long)nout * ctx->Hx + 255) / 256), (unsigned)nplanes);
@@ -1089,6 +1323,17 @@ int xinv_pass(mm_ctx* ctx, const C_t<T>* xin, T* H, long rows) {
     int rc;
     const T scale = (T)(1.0 / ((double)ctx->Lx * ctx->Py * ctx->Pz));
     KernelTimer kt(ctx, MM_K_XINV);
+    if (!pow2(ctx->Px) && ctx->Px > kBlueMin && ctx->blue_x.P == ctx->Px) {
+        const BlueArrays<T> ba = blue_arrays<T>(ctx->blue_x);
+        const int M = ctx->blue_x.M, B = blue_lines(M, sizeof(C));
+        const size_t smem = (size_t)B * M * sizeof(C);
+        rc = set_smem(ctx, (const void*)k_xinv_blue<T>, smem);
+        if (rc) return rc;
+        k_xinv_blue<T><<<(unsigned)((rows + B - 1) / B), block_threads(B * M / 8), smem, ctx->stream>>>(
+            xin, ctx->Hs, H, ctx->nx, rows, scale, ilog2(M), ilog2(B), ba.chirp, ba.filt, ba.tw);
+        MM_LAUNCH_CHECK(ctx);
+        return MM_OK;
+    }
     if (!pow2(ctx->Px)) {
         const long n = rows * ctx->nx;
         k_xinv_direct<T><<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(
@@ -1337,6 +1582,81 @@ int demag_kspace_product(mm_ctx* ctx, void* spec) {
                                                                  ctx->Py, ctx->Hx, ctx->Hs, ctx->Py2, ctx->Pz2);
     MM_LAUNCH_CHECK(ctx);
     return MM_OK;
+}
+
+namespace {
+// Bluestein data of one axis (host arithmetic in long double, exact phases)
+int blue_axis(mm_ctx* ctx, int P, Blue* bl) {
+    if (P <= kBlueMin || pow2(P)) return MM_OK;
+    int M = 1;
+    while (M < 2 * P - 1) M *= 2;
+    const long double pi = 3.141592653589793238462643383279502884L;
+    std::vector<double> chirp(2 * (size_t)P), filt(4 * (size_t)M, 0.0), tw(2 * (size_t)M);
+    std::vector<long double> cw(M), sw(M);
+    for (int m = 0; m < M; ++m) {
+        cw[m] = cosl(2.0L * pi * m / M);
+        sw[m] = sinl(2.0L * pi * m / M);
+        tw[2 * m] = (double)cw[m];
+        tw[2 * m + 1] = (double)-sw[m];
+    }
+    // exp(-i pi n^2 / P) from the exact residue of n^2 mod 2P
+    auto ph = [&](long j, long double* c, long double* sn) {
+        const long r = (j * j) % (2L * P);
+        *c = cosl(pi * r / P);
+        *sn = -sinl(pi * r / P);
+    };
+    for (int n = 0; n < P; ++n) {
+        long double c, sn;
+        ph(n, &c, &sn);
+        chirp[2 * n] = (double)c;
+        chirp[2 * n + 1] = (double)sn;
+    }
+    for (int d = 0; d < 2; ++d) {           // d = 0: DIR -1, filter b[j] = exp(+i pi j^2 / P); d = 1: its conjugate
+        std::vector<long double> vr(M, 0.0L), vi(M, 0.0L);
+        for (long j = -(P - 1); j <= P - 1; ++j) {
+            long double c, sn;
+            ph(j, &c, &sn);                 // exp(-i pi j^2 / P)
+            const int idx = (int)((j % M + M) % M);
+            vr[idx] = c;
+            vi[idx] = d == 0 ? -sn : sn;
+        }
+        for (int k = 0; k < M; ++k) {       // forward DFT of length M, scaled by 1/M
+            long double ar = 0.0L, ai = 0.0L;
+            for (int j = 0; j < M; ++j) {
+                const int m = (int)(((long)j * k) % M);
+                ar += vr[j] * cw[m] + vi[j] * sw[m];
+                ai += vi[j] * cw[m] - vr[j] * sw[m];
+            }
+            filt[2 * ((size_t)d * M + k)] = (double)(ar / M);
+            filt[2 * ((size_t)d * M + k) + 1] = (double)(ai / M);
+        }
+    }
+    bl->P = P;
+    bl->M = M;
+    auto up = [&](void** dst, const std::vector<double>& src) -> int {
+        MM_CUDA_CHECK(ctx, cudaMalloc(dst, src.size() * sizeof(double)));
+        MM_CUDA_CHECK(ctx, cudaMemcpy(*dst, src.data(), src.size() * sizeof(double), cudaMemcpyHostToDevice));
+        return MM_OK;
+    };
+    auto up32 = [&](void** dst, const std::vector<double>& src) -> int {
+        std::vector<float> f(src.begin(), src.end());
+        MM_CUDA_CHECK(ctx, cudaMalloc(dst, f.size() * sizeof(float)));
+        MM_CUDA_CHECK(ctx, cudaMemcpy(*dst, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
+        return MM_OK;
+    };
+    int rc;
+    if ((rc = up(&bl->chirp, chirp)) || (rc = up(&bl->filt, filt)) || (rc = up(&bl->tw, tw))) return rc;
+    if (ctx->prec == MM_F32 &&
+        ((rc = up32(&bl->chirp32, chirp)) || (rc = up32(&bl->filt32, filt)) || (rc = up32(&bl->tw32, tw))))
+        return rc;
+    return MM_OK;
+}
+}  // namespace
+
+int blue_prepare(mm_ctx* ctx) {
+    int rc = blue_axis(ctx, ctx->Px, &ctx->blue_x);
+    if (rc) return rc;
+    return blue_axis(ctx, ctx->Py, &ctx->blue_y);
 }
 
 int demag_setup(mm_ctx* ctx) {

@@ -64,6 +64,23 @@ struct Tables {
     long off_lx = 0, off_px = 0, off_py = 0, off_pz = 0;
 };
 
+// Bluestein (chirp-z) data of one padded axis whose length P is not a power
+// of two: transforms of P points as a convolution of length M (the power of
+// two >= 2P - 1).  Arrays at the context's precision (complex):
+//   chirp[n] = exp(-i pi n^2 / P), n < P (DIR +1 uses its conjugate);
+//   filt[d]  = FFT_M of b_d[j] = exp(-d i pi j^2 / P) on |j| < P (wrapped
+//              mod M), scaled by 1/M, for d = -1 (index 0) and +1 (index 1);
+//   tw[m]    = exp(-2 pi i m / M), m < M.
+struct Blue {
+    int P = 0, M = 0;
+    void* chirp = nullptr;   // double2 (the Newell setup runs its passes in FP64)
+    void* filt = nullptr;    // double2 [2][M]
+    void* tw = nullptr;      // double2
+    void* chirp32 = nullptr; // float2 copies for MM_F32 contexts
+    void* filt32 = nullptr;
+    void* tw32 = nullptr;
+};
+
 }  // namespace mm
 
 struct mm_ctx {
@@ -114,6 +131,7 @@ struct mm_ctx {
     mm::Control* ctl_host;    // pinned host mirror
     double* newell_host;      // [6][nz][ny][nx] real-space tensor (host copy)
     mm::Tables tw;
+    mm::Blue blue_x, blue_y;  // Bluestein data of Px and Py when they are not powers of two
 
     long launches;
     std::string err;
@@ -188,6 +206,7 @@ int demag_setup(mm_ctx* ctx);                          // K1: Newell tensor -> k
 int demag_apply(mm_ctx* ctx, const void* m, void* H);  // K2..K6
 int demag_apply_unit(mm_ctx* ctx, const void* g, void* H);  // same with Ms = 1 (adjoint)
 int demag_prepare_ff(mm_ctx* ctx);                     // float-float tables for MM_FFT_FF
+int blue_prepare(mm_ctx* ctx);                         // Bluestein data of the non-power-of-two axes
 // the tensor product of K4 on an unpruned R2C spectrum [3][Pz][Py][Hx] (in place)
 int demag_kspace_product(mm_ctx* ctx, void* spec);
 // MM_FFT_F4 (mm_f4.cu): the y forward, z product and y inverse passes fused

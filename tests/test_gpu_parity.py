@@ -366,3 +366,28 @@ def test_error_paths_underflow_and_step_cap():
     t, dt, err = mm.mm_llg_step(ctx, md, 0.0, 1e-14, mm.MM_RKF45, tol=1e-5)   # still usable
     assert t > 0 and err <= 1e-5
     mm.mm_destroy(ctx)
+
+
+EDGE_MESHES = [
+    ((512, 1, 1), (1e-9, 2e-9, 3e-9)),     # the longest x line alone
+    ((1, 512, 1), (2e-9, 1e-9, 3e-9)),     # the longest y line alone
+    ((1, 1, 512), (2e-9, 3e-9, 1e-9)),     # the longest z line alone (Pz = 1024, generic z pass)
+    ((8, 8, 512), (2e-9, 2e-9, 1e-9)),     # the largest nz on a small plane
+    ((512, 4, 2), (1e-9, 1e-9, 1e-9)),     # the longest x pass with few rows
+    ((3, 512, 2), (1e-9, 1e-9, 1e-9)),     # the longest y pass, a ragged x length
+]
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
+@pytest.mark.parametrize("n,d", EDGE_MESHES)
+def test_demag_at_the_size_limits(n, d, prec):
+    """Meshes at the extents the library accepts (512 cells along an axis)
+    and degenerate shapes (one cell thick in two directions): demag against
+    the oracle's float64 convolution."""
+    p = micromag.Problem(n, d)
+    m = wl.random_unit(n, seed=13)
+    ctx = gpu_ctx(p, prec)
+    H = torch.empty(ctx.shape3, dtype=torch.float64 if prec == mm.MM_F64 else torch.float32, device="cuda")
+    mm.mm_demag_field(ctx, dev(m, prec), H)
+    assert rel_l2(host(H), p.demag_fft(m)) < TOL[prec]
+    mm.mm_destroy(ctx)

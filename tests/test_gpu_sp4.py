@@ -1,4 +1,4 @@
-"""Meshes whose sizes are not powers of two (direct-DFT passes) through the C
+"""Meshes whose sizes are not powers of two (direct-DFT and Bluestein passes) through the C
 ABI against the oracle, and an SP4-shaped problem (the paper's validation
 geometry): a 100 x 25 x 1 permalloy film of 5 x 5 x 3 nm cells, minimised
 from m = (1, 0.25, 0.1) and then driven by the field
@@ -35,8 +35,12 @@ def rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
+# padded lengths up to 64 take the direct DFT, longer ones the Bluestein passes
+# (100 x 50: Px = 200, Py = 100; 350 x 70: Px = 700 with M = 2048; 36 x 200:
+# Py = 400)
 MESHES = [((100, 25, 1), (5e-9, 5e-9, 3e-9)), ((12, 10, 2), (2e-9, 3e-9, 2.5e-9)), ((7, 5, 4), (3e-9, 2e-9, 2e-9)),
-          ((33, 1, 1), (2e-9, 2e-9, 2e-9)), ((1, 18, 2), (2e-9, 2e-9, 2e-9))]
+          ((33, 1, 1), (2e-9, 2e-9, 2e-9)), ((1, 18, 2), (2e-9, 2e-9, 2e-9)), ((100, 50, 2), (5e-9, 5e-9, 3e-9)),
+          ((350, 70, 1), (2e-9, 2e-9, 2e-9)), ((36, 200, 4), (3e-9, 2e-9, 2e-9))]
 
 
 @pytest.mark.parametrize("prec", [mm.MM_F64, mm.MM_F32], ids=["f64", "f32"])
@@ -111,3 +115,29 @@ def test_sp4_field1_one_ns_fp32_tracks_fp64():
     print("SP4 field 1: <m> at 1 ns", traces[mm.MM_F64][-1], "max |<m>_f32 - <m>_f64|", d)
     assert traces[mm.MM_F64][-1][0] < 0          # the film has switched: <m_x> < 0 at 1 ns
     assert d < 2e-2
+
+
+def test_bluestein_pass_time_on_a_350_cell_film():
+    """The Bluestein passes on a 350 x 350 x 4 film (Px = Py = 700, M =
+    2048): demag against the oracle at the FP32 tolerance, and the time per
+    evaluation (printed)."""
+    n, d = (350, 350, 4), (2e-9, 2e-9, 2e-9)
+    p = micromag.Problem(n, d)
+    m = wl.random_unit(n, seed=21)
+    ctx = mm.mm_init_mesh(*n, *d, precision=mm.MM_F32)
+    mm.mm_set_material(ctx, 8e5, 1.3e-11, 0.02, 0.0)
+    md = dev(m, mm.MM_F32)
+    H = torch.empty_like(md)
+    mm.mm_demag_field(ctx, md, H)
+    assert rel(H.double().cpu().numpy(), p.demag_fft(m)) < 1e-5
+    for _ in range(3):
+        mm.mm_demag_field(ctx, md, H)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(20):
+        mm.mm_demag_field(ctx, md, H)
+    b.record()
+    torch.cuda.synchronize()
+    print(f"350 x 350 x 4 FP32 demag: {a.elapsed_time(b) / 20:.3f} ms per evaluation")
+    mm.mm_destroy(ctx)
