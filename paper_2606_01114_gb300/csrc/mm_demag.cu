@@ -30,6 +30,7 @@
 #include "mm_fft.cuh"
 #include "mm_ff.cuh"
 #include "mm_regfft.cuh"
+#include "mm_tma.cuh"
 
 namespace mm {
 namespace {
@@ -975,6 +976,126 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// K3 / K5, TMA-fed (Py = L = 512 or 1024, the pruning of the product path):
+// the same four-step arithmetic as k_cols_reg, with the column tiles
+// streamed into shared memory by the copy engine.  A persistent block (one
+// per SM: two 64 KB stages at L = 1024) walks tiles of kYB columns of one
+// plane, tile = cx + ntx p.  Per tile:
+//   wait for its stage's mbarrier (the tile's nin rows, in boxes of 256
+//   rows x kYB columns, row-major [row][b]);
+//   level 1 reads its inputs from the stage; barrier; writes its twiddled
+//   outputs back into the same stage buffer (the transpose, XOR-swizzled
+//   as in k_cols_reg); barrier; level 2 reads them; barrier;
+//   thread 0 re-arms the stage and issues the copies of tile + 2 grid;
+//   level 2's DFT and its global stores overlap that copy and the one
+//   already in flight into the other stage.
+// The register passes leave DRAM idle while a block computes and have two
+// blocks per SM to cover it; here the next tile is always landing.
+// Waits are bounded: a wait that gives up raises TIMEOUT in the device
+// status, waits (bounded) for the copies still in flight and returns.
+constexpr int kYB = 8;          // columns per tile (64-byte rows)
+constexpr int kYStages = 2;
+constexpr long kYWaitLimit = 1L << 24;
+
+template <int L1, int L2, int DIR, bool PIN, bool POUT>
+__global__ void __launch_bounds__(kYB * (L1 > L2 ? L1 : L2), L1 * L2 >= 1024 ? 1 : 2)
+    k_cols_tma(const __grid_constant__ CUtensorMap tin, float2* __restrict__ out, int Hx, int ntx, int ntiles,
+               long rs_out, long out_plane, const float2* __restrict__ tw, int* __restrict__ status) {
+    constexpr int L = L1 * L2, B = kYB, S = kYStages;
+    constexpr int NIN = PIN ? L / 2 : L;
+    constexpr int BOX = NIN < 256 ? NIN : 256;
+    constexpr int NBOX = NIN / BOX;
+    constexpr uint32_t TX = (uint32_t)NIN * B * sizeof(float2);
+    constexpr int m = (16 / B) - 1;
+    static_assert(NIN % BOX == 0, "the rows split into whole boxes");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // copy destinations 128-byte aligned (the launch adds 128 bytes of slack)
+    unsigned char* sm = smem_raw + ((128u - (tma::smem_addr(smem_raw) & 127u)) & 127u);
+    float2* st = reinterpret_cast<float2*>(sm);                                    // [S][L][B]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + (size_t)S * L * B * sizeof(float2));
+    const int tid = threadIdx.x;
+    const int b = tid % B, t = tid / B;
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) tc5::mbar_init(tma::smem_addr(&bar[s]), 1);
+        tma::fence_init();
+    }
+    __syncthreads();
+    auto issue = [&](int tile, int s) {
+        const int cx = tile % ntx, p = tile / ntx;
+        const uint32_t mb = tma::smem_addr(&bar[s]);
+        tma::expect_tx(mb, TX);
+#pragma unroll
+        for (int q = 0; q < NBOX; ++q)
+            tma::load_3d(tma::smem_addr(st + ((size_t)s * L + q * BOX) * B), &tin, 2 * B * cx, q * BOX, p, mb);
+    };
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            const int tile = blockIdx.x + s * gridDim.x;
+            if (tile < ntiles) issue(tile, s);
+        }
+    }
+    int i = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+        const int s = i % S;
+        float2* Sb = st + (size_t)s * L * B;
+        const bool ok = tc5::mbar_wait(tma::smem_addr(&bar[s]), (uint32_t)((i / S) & 1), kYWaitLimit);
+        float2 v[L1];
+        if (t < L2) {
+            constexpr int NI = PIN ? L1 / 2 : L1;
+#pragma unroll
+            for (int n1 = 0; n1 < NI; ++n1) v[n1] = Sb[(t + L2 * n1) * B + b];
+        }
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicCAS(status, 0, (int)MM_ERR_TIMEOUT);
+                for (int j = i; j < i + S; ++j) {
+                    if (blockIdx.x + j * gridDim.x < ntiles)
+                        tc5::mbar_wait(tma::smem_addr(&bar[j % S]), (uint32_t)((j / S) & 1), kYWaitLimit);
+                }
+            }
+            return;
+        }
+        if (t < L2) {
+            dif<L1, DIR, PIN>(v);
+#pragma unroll
+            for (int k1 = 0; k1 < L1; ++k1) {
+                float2 y = v[dif_pos<L1>(k1)];
+                if (k1 > 0) {
+                    float2 w = tw[t * k1];
+                    if (DIR > 0) w.y = -w.y;
+                    y = cmul(y, w);
+                }
+                Sb[((k1 * L2) + (t ^ (k1 & m))) * B + b] = y;
+            }
+        }
+        __syncthreads();
+        float2 u[L2];
+        if (t < L1) {
+#pragma unroll
+            for (int n2 = 0; n2 < L2; ++n2) u[n2] = Sb[((t * L2) + (n2 ^ (t & m))) * B + b];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const int nt = tile + S * gridDim.x;
+            if (nt < ntiles) {
+                tma::fence_async();
+                issue(nt, s);
+            }
+        }
+        if (t < L1) {
+            dif<L2, DIR, false>(u);
+            const int cx = tile % ntx, p = tile / ntx;
+            const int col = cx * B + b;
+            constexpr int NOUT = POUT ? L2 / 2 : L2;
+            if (col < Hx) {
+                float2* ob = out + (long)p * out_plane + col;
+#pragma unroll
+                for (int k2 = 0; k2 < NOUT; ++k2) ob[(long)(t + L1 * k2) * rs_out] = u[dif_pos<L2>(k2)];
+            }
+        }
+    }
+}
+
 // K1 tail: keep the real octant of the transformed component, at precision T.
 template <typename T>
 __global__ void k_extract(const double2* __restrict__ X, int Py, int Hs, int Hx, int Py2, int Pz2,
@@ -1187,6 +1308,91 @@ int try_cols_reg(mm_ctx* ctx, const float2* in, float2* out, int L, int nplanes,
     }
 }
 
+// TMA-fed y passes: descriptors of the pass inputs bufA ([3 nz][ny][Hs]
+// complex, the x pass's output) and bufB ([3 nz][Py][Hs], the z pass's
+// output), encoded once per context, and the persistent grid of each
+// direction (SMs x resident blocks).  Any failure leaves the register passes.
+template <int L1, int L2, int DIR>
+constexpr auto cols_tma_fn() {
+    return k_cols_tma<L1, L2, DIR, (DIR < 0), (DIR > 0)>;
+}
+template <int L1, int L2>
+size_t cols_tma_smem() {
+    return (size_t)kYStages * L1 * L2 * kYB * sizeof(float2) + kYStages * sizeof(uint64_t) + 128;
+}
+
+template <int L1, int L2>
+int ymaps_prepare_t(mm_ctx* ctx) {
+    ctx->ymap_state = -1;
+    const size_t smem = cols_tma_smem<L1, L2>();
+    const void* fns[2] = {(const void*)cols_tma_fn<L1, L2, -1>(), (const void*)cols_tma_fn<L1, L2, +1>()};
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
+        cudaGetLastError();
+        return MM_OK;
+    }
+    for (int d = 0; d < 2; ++d) {
+        int per_sm = 0;
+        if (cudaFuncSetAttribute(fns[d], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[d], kYB * (L1 > L2 ? L1 : L2), smem) !=
+                cudaSuccess || per_sm < 1) {
+            cudaGetLastError();
+            return MM_OK;
+        }
+        ctx->ymap_grid[d] = nsm * per_sm;
+    }
+    const uint64_t Hs = (uint64_t)ctx->Hs, planes = 3ull * ctx->nz;
+    const uint64_t rows[2] = {(uint64_t)ctx->ny, (uint64_t)ctx->Py};
+    void* bases[2] = {ctx->bufA, ctx->bufB};
+    for (int d = 0; d < 2; ++d) {
+        const uint32_t box_rows = (uint32_t)(rows[d] < 256 ? rows[d] : 256);
+        if (!tma_encode_3d(ctx->ymap[d], bases[d], 2 * Hs, rows[d], planes, Hs * sizeof(float2),
+                           rows[d] * Hs * sizeof(float2), 2 * kYB, box_rows, 1))
+            return MM_OK;
+    }
+    ctx->ymap_state = 1;
+    return MM_OK;
+}
+
+// the TMA-fed pass when the context qualifies (FP32, plain mode, Py = 512 or
+// 1024, the context's own buffers in the product geometry); *done = false
+// leaves the register passes
+template <int DIR>
+int try_cols_tma(mm_ctx* ctx, const float2* in, float2* out, int L, int nplanes, const ColGeom& g, const float2* tw,
+                 bool* done) {
+    *done = false;
+    if (ctx->fft_mode != 0 || (L != 512 && L != 1024) || ctx->Py != L) return MM_OK;
+    const bool canonical = DIR < 0 ? ((const void*)in == ctx->bufA && (void*)out == ctx->bufB &&
+                                      g.in_inner == (long)ctx->ny * ctx->Hs && g.out_inner == (long)L * ctx->Hs)
+                                   : ((const void*)in == ctx->bufB && (void*)out == ctx->bufA &&
+                                      g.in_inner == (long)L * ctx->Hs && g.out_inner == (long)ctx->ny * ctx->Hs);
+    if (!canonical || nplanes != 3 * ctx->nz || g.n_inner != nplanes || g.in_outer != 0 || g.out_outer != 0 ||
+        g.rs_in != ctx->Hs || g.rs_out != ctx->Hs)
+        return MM_OK;
+    if (ctx->ymap_state == 0) {
+        int rc = L == 1024 ? ymaps_prepare_t<32, 32>(ctx) : ymaps_prepare_t<32, 16>(ctx);
+        if (rc) return rc;
+    }
+    if (ctx->ymap_state != 1) return MM_OK;
+    alignas(64) CUtensorMap map;
+    std::memcpy(&map, ctx->ymap[DIR < 0 ? 0 : 1], sizeof(map));
+    const int ntx = (ctx->Hx + kYB - 1) / kYB, ntiles = ntx * nplanes;
+    const int grid = ctx->ymap_grid[DIR < 0 ? 0 : 1] < ntiles ? ctx->ymap_grid[DIR < 0 ? 0 : 1] : ntiles;
+    int* status = &ctx->ctl->status;
+    if (L == 1024) {
+        auto fn = cols_tma_fn<32, 32, DIR>();
+        fn<<<grid, kYB * 32, cols_tma_smem<32, 32>(), ctx->stream>>>(map, out, ctx->Hx, ntx, ntiles, g.rs_out,
+                                                                     g.out_inner, tw, status);
+    } else {
+        auto fn = cols_tma_fn<32, 16, DIR>();
+        fn<<<grid, kYB * 32, cols_tma_smem<32, 16>(), ctx->stream>>>(map, out, ctx->Hx, ntx, ntiles, g.rs_out,
+                                                                     g.out_inner, tw, status);
+    }
+    *done = true;
+    MM_LAUNCH_CHECK(ctx);
+    return MM_OK;
+}
+
 template <typename T, int DIR>
 int run_cols(mm_ctx* ctx, const C_t<T>* in, C_t<T>* out, int L, int nin, int nout, int nplanes, ColGeom g,
              const C_t<T>* tw) {
@@ -1217,7 +1423,9 @@ int run_cols(mm_ctx* ctx, const C_t<T>* in, C_t<T>* out, int L, int nin, int nou
             return tc_cols(ctx, in, out, L, DIR, nplanes, g, tw);
         if (product_pruning) {
             bool done = false;
-            int rc = try_cols_reg<DIR>(ctx, in, out, L, nplanes, g, tw, &done, 0, ctx->Hx);
+            int rc = try_cols_tma<DIR>(ctx, in, out, L, nplanes, g, tw, &done);
+            if (done || rc) return rc;
+            rc = try_cols_reg<DIR>(ctx, in, out, L, nplanes, g, tw, &done, 0, ctx->Hx);
             if (done) return rc;
         }
     }
@@ -1677,6 +1885,41 @@ int demag_apply_unit(mm_ctx* ctx, const void* g, void* H) {
         return apply<double>(ctx, (const double*)g, (double*)H, true);
     }
     return apply<float>(ctx, (const float*)g, (float*)H, true);
+}
+
+}  // namespace mm
+
+namespace mm {
+
+// cuTensorMapEncodeTiled, looked up once through the runtime (no libcuda link)
+bool tma_encode_3d(void* map128, const void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t s1, uint64_t s2,
+                   uint32_t b0, uint32_t b1, uint32_t b2) {
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Encode enc = []() -> Encode {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return (Encode)fn;
+    }();
+    if (!enc) return false;
+    alignas(64) CUtensorMap map;
+    const cuuint64_t dims[3] = {d0, d1, d2};
+    const cuuint64_t strides[2] = {s1, s2};
+    const cuuint32_t box[3] = {b0, b1, b2};
+    const cuuint32_t es[3] = {1, 1, 1};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    std::memcpy(map128, &map, sizeof(map));
+    return true;
 }
 
 }  // namespace mm

@@ -132,6 +132,12 @@ struct mm_ctx {
     double* newell_host;      // [6][nz][ny][nx] real-space tensor (host copy)
     mm::Tables tw;
     mm::Blue blue_x, blue_y;  // Bluestein data of Px and Py when they are not powers of two
+    // TMA descriptors (CUtensorMap bytes) of the y passes' inputs, FP32
+    // contexts with Py = 512 or 1024: [0] bufA as [3 nz][ny][Hs] complex,
+    // [1] bufB as [3 nz][Py][Hs]; encoded on first use
+    alignas(64) unsigned char ymap[2][128];
+    int ymap_state;           // 0 not tried, 1 ready, -1 not available (register passes instead)
+    int ymap_grid[2];         // persistent grids of the TMA-fed y forward [0] and inverse [1] passes
 
     long launches;
     std::string err;

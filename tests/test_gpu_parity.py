@@ -95,6 +95,31 @@ def test_demag_matches_oracle(n, d, prec):
     mm.mm_destroy(ctx)
 
 
+# Py = 1024 and 512 take the TMA-fed y passes in FP32 (8-column tiles, the
+# last one ragged: Hx = 25 and 41); the x passes here are the direct-DFT
+# (Px = 48) and Bluestein (Px = 80) ones, and nz = 1 takes the Pz = 1 z pass
+TMA_Y_MESHES = [
+    ((24, 512, 2), (2e-9, 2e-9, 3e-9)),
+    ((40, 256, 4), (3e-9, 2e-9, 2e-9)),
+    ((16, 512, 1), (2e-9, 2e-9, 1e-9)),
+]
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
+@pytest.mark.parametrize("n,d", TMA_Y_MESHES)
+def test_demag_tma_y_pass_meshes_match_oracle(n, d, prec):
+    p = oracle_problem(n, d)
+    m = wl.random_unit(n, seed=7)
+    ctx = gpu_ctx(p, prec)
+    H = torch.empty(ctx.shape3, dtype=torch.float64 if prec == mm.MM_F64 else torch.float32, device="cuda")
+    mm.mm_demag_field(ctx, dev(m, prec), H)
+    got, ref = host(H), p.demag_fft(m)
+    assert rel_l2(got, ref) < TOL[prec]
+    # every cell, against the field's scale
+    assert np.max(np.abs(got - ref)) < 10 * TOL[prec] * np.max(np.abs(ref))
+    mm.mm_destroy(ctx)
+
+
 @pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
 def test_demag_per_cell_ms_with_vacuum(prec):
     n, d = (32, 16, 4), (2e-9, 3e-9, 1.5e-9)
