@@ -597,8 +597,11 @@ __device__ __forceinline__ void zconv_product(float2 (&v)[PZ], const float2* S, 
     }
 }
 
+// (PZ = 32: at most 80 registers, 6 blocks per SM by shared memory; at the
+// compiler's own 126 registers only 5 fit, and the pass took 126 us against
+// about 112 on the 512 x 512 x 16 film)
 template <int PZ>
-__global__ void __launch_bounds__(3 * kZB)
+__global__ void __launch_bounds__(3 * kZB, PZ >= 32 ? 7 : 8)
     k_zconv_reg(float2* buf, const float* __restrict__ kern, int Py, int Hs, int c0, int Hx, int Py2) {
     constexpr int NZ = PZ > 1 ? PZ / 2 : 1;
     constexpr int PZ2 = PZ / 2 + 1;
@@ -924,6 +927,122 @@ __global__ void __launch_bounds__(128, 7)
     });
 }
 
+// K6 for L = 512 (nx = 512), TMA-fed: the arithmetic of k_xinv_pk<16, 32>,
+// with tiles of kXB spectrum rows (Hs = 528, 16.5 KB, contiguous) streamed
+// into shared memory by one 1-D bulk copy each, a 2-stage mbarrier ring per
+// persistent block, and the level-1 transpose written in place over the
+// stage's input.  Per tile: wait; level-1 loads from the stage with the
+// complex-to-real packing; barrier (past it, every thread has finished the
+// previous tile, so thread 0 re-arms that tile's stage with the next tile);
+// level-1 DFT and transpose into the stage; barrier; level 2 and the global
+// stores, which overlap the copy in flight.  Bounded waits as in k_cols_tma.
+// (The same ring for K2 ran 37.0 us against 33.5 us for k_xfwd_reg: that
+// pass keeps its direct loads.)
+constexpr int kXB = 4;        // rows per tile
+constexpr int kXHs = 528;     // spectrum row stride for nx = 512
+constexpr long kTmaWaitLimit = 1L << 24;   // polls of a TMA-fed pass's mbarrier before it gives up
+
+__global__ void __launch_bounds__(128, 6)
+    k_xinv_tma(const float2* __restrict__ in, float* __restrict__ out, long rows, int ntiles, float scale,
+               const float2* __restrict__ twL, const float2* __restrict__ twP, int* __restrict__ status) {
+    constexpr int L1 = 16, L2 = 32, L = L1 * L2, B = kXB, NX = L, S = 2, HS = kXHs;
+    constexpr int STAGE = B * HS;                  // float2 per stage (>= B L)
+    static_assert(B * HS >= B * L && (B * HS * 8) % 128 == 0, "stage holds the input tile and the transpose");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* sm = smem_raw + ((128u - (tma::smem_addr(smem_raw) & 127u)) & 127u);
+    float2* st = reinterpret_cast<float2*>(sm);                                    // [S][B][HS]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + (size_t)S * STAGE * sizeof(float2));
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int q = 0; q < S; ++q) tc5::mbar_init(tma::smem_addr(&bar[q]), 1);
+        tma::fence_init();
+    }
+    __syncthreads();
+    auto issue = [&](int tile, int q) {
+        const long r0 = (long)tile * B;
+        const long nr = rows - r0 < B ? rows - r0 : B;
+        const uint32_t bytes = (uint32_t)(nr * HS * sizeof(float2));
+        const uint32_t mb = tma::smem_addr(&bar[q]);
+        tma::expect_tx(mb, bytes);
+        tma::load_1d(tma::smem_addr(st + (size_t)q * STAGE), in + r0 * HS, bytes, mb);
+    };
+    if (tid == 0) {
+        for (int q = 0; q < S; ++q) {
+            const int tile = blockIdx.x + q * gridDim.x;
+            if (tile < ntiles) issue(tile, q);
+        }
+    }
+    int i = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+        const int sidx_ = i % S;
+        float2* Sb = st + (size_t)sidx_ * STAGE;
+        const long r0 = (long)tile * B;
+        const bool ok = tc5::mbar_wait(tma::smem_addr(&bar[sidx_]), (uint32_t)((i / S) & 1), kTmaWaitLimit);
+        // level 1 with the packing folded into the loads (as k_xinv_pk)
+        const int t = tid % L2, b1 = tid / L2;
+        const bool act = r0 + b1 < rows;
+        const float2* irow = Sb + b1 * HS;
+        const float2 wt = cconj(twP[t]);
+        float2 v[L1];
+        static_for<0, L1>([&](auto N1) {
+            constexpr int n1 = decltype(N1)::value;
+            const int n = t + L2 * n1;
+            const float2 xk = act ? irow[n] : make_float2(0.f, 0.f);
+            const float2 xc = act ? irow[L - n] : make_float2(0.f, 0.f);
+            const float2 c = cconj(xc);
+            const float2 e = cscale(cadd(xk, c), 0.5f);
+            float2 o = cmul(cscale(csub(xk, c), 0.5f), wt);
+            if constexpr (n1 > 0) {
+                constexpr double cc = cos2pi(n1, 2 * L1), ss = sin2pi(n1, 2 * L1);
+                o = cmul(o, make_float2((float)cc, (float)ss));
+            }
+            v[n1] = make_float2(e.x - o.y, e.y + o.x);
+        });
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicCAS(status, 0, (int)MM_ERR_TIMEOUT);
+                for (int j = i; j < i + S; ++j) {
+                    if (blockIdx.x + j * gridDim.x < ntiles)
+                        tc5::mbar_wait(tma::smem_addr(&bar[j % S]), (uint32_t)((j / S) & 1), kTmaWaitLimit);
+                }
+            }
+            return;
+        }
+        // every thread is past the previous tile, whose stage now takes tile i + 1
+        if (tid == 0 && i > 0) {
+            const int nt = tile + gridDim.x;
+            if (nt < ntiles) {
+                tma::fence_async();
+                issue(nt, (i + 1) % S);
+            }
+        }
+        dif<L1, +1, false>(v);
+#pragma unroll
+        for (int k1 = 0; k1 < L1; ++k1) {
+            float2 y = v[dif_pos<L1>(k1)];
+            if (k1 > 0) y = cmul(y, cconj(twL[t * k1]));
+            Sb[b1 * L + xsw<L1, L2>(k1, t)] = y;
+        }
+        __syncthreads();
+        if (tid < B * L1) {
+            const int k1 = tid % L1, b2 = tid / L1;
+            float2 u[L2];
+#pragma unroll
+            for (int n2 = 0; n2 < L2; ++n2) u[n2] = Sb[b2 * L + xsw<L1, L2>(k1, n2)];
+            dif<L2, +1, false>(u);
+            const long r = r0 + b2;
+            if (r < rows) {
+                float2* op = reinterpret_cast<float2*>(out + r * NX);
+#pragma unroll
+                for (int k2 = 0; k2 < L2 / 2; ++k2) {
+                    const float2 z = u[dif_pos<L2>(k2)];
+                    op[k1 + L1 * k2] = make_float2(z.x * scale, z.y * scale);
+                }
+            }
+        }
+    }
+}
+
 // K3 / K5 for L = L1 x L2 (64 <= L <= 1024): four-step transform of B
 // columns.  Level 1: thread t < L2 of a column holds x[t + L2 n1], n1 < L1,
 // (upper half zero when PIN), DFT over n1, twiddle w_L^(t k1), store to
@@ -995,7 +1114,6 @@ __global__ void __launch_bounds__(256)
 // status, waits (bounded) for the copies still in flight and returns.
 constexpr int kYB = 8;          // columns per tile (64-byte rows)
 constexpr int kYStages = 2;
-constexpr long kYWaitLimit = 1L << 24;
 
 template <int L1, int L2, int DIR, bool PIN, bool POUT>
 __global__ void __launch_bounds__(kYB * (L1 > L2 ? L1 : L2), L1 * L2 >= 1024 ? 1 : 2)
@@ -1038,7 +1156,7 @@ __global__ void __launch_bounds__(kYB * (L1 > L2 ? L1 : L2), L1 * L2 >= 1024 ? 1
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
         const int s = i % S;
         float2* Sb = st + (size_t)s * L * B;
-        const bool ok = tc5::mbar_wait(tma::smem_addr(&bar[s]), (uint32_t)((i / S) & 1), kYWaitLimit);
+        const bool ok = tc5::mbar_wait(tma::smem_addr(&bar[s]), (uint32_t)((i / S) & 1), kTmaWaitLimit);
         float2 v[L1];
         if (t < L2) {
             constexpr int NI = PIN ? L1 / 2 : L1;
@@ -1050,7 +1168,7 @@ __global__ void __launch_bounds__(kYB * (L1 > L2 ? L1 : L2), L1 * L2 >= 1024 ? 1
                 atomicCAS(status, 0, (int)MM_ERR_TIMEOUT);
                 for (int j = i; j < i + S; ++j) {
                     if (blockIdx.x + j * gridDim.x < ntiles)
-                        tc5::mbar_wait(tma::smem_addr(&bar[j % S]), (uint32_t)((j / S) & 1), kYWaitLimit);
+                        tc5::mbar_wait(tma::smem_addr(&bar[j % S]), (uint32_t)((j / S) & 1), kTmaWaitLimit);
                 }
             }
             return;
@@ -1227,6 +1345,26 @@ int try_xinv_reg(mm_ctx* ctx, const float2* in, float* out, long rows, float sca
         case 512: return launch_xinv_reg<32, 16>(ctx, in, out, rows, scale, twL, twP);
         default: *done = false; return MM_OK;
     }
+}
+
+// TMA-fed x inverse (FP32, nx = 512): shared memory per block, and the
+// persistent grid (SMs x resident blocks), found once per context
+constexpr size_t kXinvTmaSmem = 2 * (size_t)kXB * kXHs * sizeof(float2) + 2 * sizeof(uint64_t) + 128;
+
+void xtma_prepare(mm_ctx* ctx) {
+    ctx->xtma_state = -1;
+    int nsm = 0, per = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess ||
+        cudaFuncSetAttribute((const void*)k_xinv_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kXinvTmaSmem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void*)k_xinv_tma, 128, kXinvTmaSmem) !=
+            cudaSuccess ||
+        per < 1) {
+        cudaGetLastError();
+        return;
+    }
+    ctx->xtma_grid = nsm * per;
+    ctx->xtma_state = 1;
 }
 
 // x-forward over `rows` rows
@@ -1555,6 +1693,19 @@ int xinv_pass(mm_ctx* ctx, const C_t<T>* xin, T* H, long rows) {
     } else {
         const int L = ctx->Lx;
         if constexpr (sizeof(T) == 4) {
+            if (L == 512 && ctx->Hs == kXHs) {
+                if (ctx->xtma_state == 0) xtma_prepare(ctx);
+                if (ctx->xtma_state == 1) {
+                    const int ntiles = (int)((rows + kXB - 1) / kXB);
+                    const int grid = ctx->xtma_grid < ntiles ? ctx->xtma_grid : ntiles;
+                    k_xinv_tma<<<grid, 128, kXinvTmaSmem, ctx->stream>>>(
+                        (const float2*)xin, (float*)H, rows, ntiles, (float)scale,
+                        (const float2*)table<T>(ctx, ctx->tw.off_lx), (const float2*)table<T>(ctx, ctx->tw.off_px),
+                        &ctx->ctl->status);
+                    MM_LAUNCH_CHECK(ctx);
+                    return MM_OK;
+                }
+            }
             bool done = false;
             if (L >= 64) {
                 rc = try_xinv_reg(ctx, (const float2*)xin, (float*)H, rows, (float)scale,

@@ -138,6 +138,8 @@ struct mm_ctx {
     alignas(64) unsigned char ymap[2][128];
     int ymap_state;           // 0 not tried, 1 ready, -1 not available (register passes instead)
     int ymap_grid[2];         // persistent grids of the TMA-fed y forward [0] and inverse [1] passes
+    int xtma_state;           // TMA-fed x inverse (nx = 512): 0 not tried, 1 ready, -1 not available
+    int xtma_grid;            // its persistent grid
 
     long launches;
     std::string err;

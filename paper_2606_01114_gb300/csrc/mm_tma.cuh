@@ -46,6 +46,14 @@ __device__ __forceinline__ void load_3d(uint32_t dst, const CUtensorMap* map, in
         : "memory");
 }
 
+// `bytes` contiguous bytes (a multiple of 16, both addresses 16-byte
+// aligned) from global memory into shared memory at dst, completing on mbar
+__device__ __forceinline__ void load_1d(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+
 }  // namespace tma
 
 // Host: encode a 3-D FP32 tensor map over dims (d0 innermost, d1, d2) with

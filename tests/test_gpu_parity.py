@@ -97,11 +97,15 @@ def test_demag_matches_oracle(n, d, prec):
 
 # Py = 1024 and 512 take the TMA-fed y passes in FP32 (8-column tiles, the
 # last one ragged: Hx = 25 and 41); the x passes here are the direct-DFT
-# (Px = 48) and Bluestein (Px = 80) ones, and nz = 1 takes the Pz = 1 z pass
+# (Px = 48) and Bluestein (Px = 80) ones, and nz = 1 takes the Pz = 1 z pass.
+# nx = 512 takes the TMA-fed x passes (4-row tiles; 3 x 1 x 3 = 9 rows leave
+# a last tile of one row)
 TMA_Y_MESHES = [
     ((24, 512, 2), (2e-9, 2e-9, 3e-9)),
     ((40, 256, 4), (3e-9, 2e-9, 2e-9)),
     ((16, 512, 1), (2e-9, 2e-9, 1e-9)),
+    ((512, 8, 2), (2e-9, 2e-9, 3e-9)),
+    ((512, 3, 1), (2e-9, 3e-9, 2e-9)),
 ]
 
 
