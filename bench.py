@@ -107,7 +107,8 @@ def load_peaks():
 # the sources each timed kernel family is compiled from: stored ncu traffic
 # stays valid while these files are unchanged
 KERNEL_SOURCES = {
-    "demag": ("mm_demag.cu", "mm_fft.cuh", "mm_regfft.cuh", "mm_ff.cuh", "mm_internal.cuh"),
+    "demag": ("mm_demag.cu", "mm_fft.cuh", "mm_regfft.cuh", "mm_ff.cuh", "mm_tma.cuh", "mm_tcgen05.cuh",
+              "mm_internal.cuh"),
     "stage": ("mm_llg.cu", "mm_fields.cuh", "mm_ff.cuh", "mm_internal.cuh"),
 }
 FAMILY = {"xfwd": "demag", "yfwd": "demag", "zconv": "demag", "yinv": "demag", "xinv": "demag", "stage": "stage"}
@@ -188,7 +189,7 @@ def ingest_ncu(csv_path, precision, workload):
             if not mt or not mt.group(1).startswith(prefix):
                 continue
             if k in ("yfwd", "yinv"):
-                # k_cols_reg<L1, L2, DIR, PIN, POUT>: DIR is the third argument
+                # k_cols_reg / k_cols_tma<L1, L2, DIR, PIN, POUT>: DIR is the third argument
                 direction = int(mt.group(2).split(",")[2].replace("(int)", "").strip())
                 if (direction < 0) != (k == "yfwd"):
                     continue
