@@ -121,7 +121,11 @@ int mm_set_dmi(mm_ctx* ctx, double D, int type);
  * taken at each step from the current material.  Errors: INVALID_ARG. */
 int mm_set_stt(mm_ctx* ctx, double J, double P, double Lambda, double eps_prime, const double p[3], double d);
 
-/* H = demagnetisation field of m (Eq. 4), both device [3][nz][ny][nx]. */
+/* H = demagnetisation field of m (Eq. 4), both device [3][nz][ny][nx].
+ * FP32 contexts with ny = 256 or 512, or nx = 512, run some passes fed by
+ * the copy engine (TMA) with bounded waits; a wait that gives up raises
+ * TIMEOUT in the device status, which mm_llg_step, mm_relax and
+ * mm_minimize_bb report (no GPU fault is involved). */
 int mm_demag_field(mm_ctx* ctx, const void* m, void* H);
 
 /* H = exchange field of m (Eq. 2), 6-point stencil, harmonic-mean A,
@@ -138,7 +142,7 @@ int mm_effective_field(mm_ctx* ctx, const void* m, void* H);
  *     max_cells |m5 - m4| <= tol; on return *t is advanced by the accepted
  *     step, *dt holds the proposed next step and *err_out the accepted error.
  * m is renormalised after the step.  Errors: INVALID_ARG, NONFINITE,
- * DT_UNDERFLOW, CUDA. */
+ * DT_UNDERFLOW, TIMEOUT (a bounded device wait gave up), CUDA. */
 int mm_llg_step(mm_ctx* ctx, void* m, double* t, double* dt, int method, double tol,
                 double* err_out);
 
@@ -156,7 +160,7 @@ int mm_llg_step_host(mm_ctx* ctx, void* m_host, double* t, double* dt, int metho
  * time reaches t_max.  *t_out, *steps_out (nullable) receive the simulated
  * time and accepted step count.  Step-size control stays on the device.
  * Errors: NOT_CONVERGED when max_steps is reached first, NONFINITE,
- * DT_UNDERFLOW, CUDA. */
+ * DT_UNDERFLOW, TIMEOUT (a bounded device wait gave up), CUDA. */
 int mm_relax(mm_ctx* ctx, void* m, double t_max, double torque_tol, long max_steps,
              double* t_out, long* steps_out);
 
@@ -171,7 +175,8 @@ int mm_relax(mm_ctx* ctx, void* m, double t_max, double torque_tol, long max_ste
  * (tested every step on the device) or after max_iter steps; *iters_out
  * (nullable) receives the steps taken.  m (device, in place) holds the last
  * state in either case.  Uses the integrator's scratch buffers.  Errors:
- * NOT_CONVERGED (max_iter reached first), NONFINITE, INVALID_ARG, CUDA. */
+ * NOT_CONVERGED (max_iter reached first), NONFINITE, INVALID_ARG, TIMEOUT (a
+ * bounded device wait gave up), CUDA. */
 int mm_minimize_bb(mm_ctx* ctx, void* m, double torque_tol, long max_iter, long* iters_out);
 
 /* E_out[0..4] = demag, exchange, anisotropy, Zeeman, DMI energy of m in J

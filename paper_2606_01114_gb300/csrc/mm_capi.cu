@@ -199,6 +199,7 @@ int device_status(mm_ctx* ctx) {
     int st = ctx->ctl_host->status;
     if (st == MM_ERR_NONFINITE) return fail(ctx, st, "NaN or Inf in the magnetisation");
     if (st == MM_ERR_DT_UNDERFLOW) return fail(ctx, st, "RKF45 step fell below 1e-20 s");
+    if (st == MM_ERR_TIMEOUT) return fail(ctx, st, "a bounded device wait (TMA-fed demag pass) gave up");
     if (st) return fail(ctx, st, "device status %d", st);
     return MM_OK;
 }
