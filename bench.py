@@ -142,6 +142,10 @@ def ncu_traffic(kernel, precision):
     return float(e["bytes_per_launch"])
 
 
+# a kernel's name in an ncu export, with its template arguments when it has any
+KNAME = r"(k_\w+)(?:<([^>]*)>)?\("
+
+
 def ingest_ncu(csv_path, precision, workload):
     """Update profiles/traffic.json from an ncu raw CSV export
     (``ncu -i rep --page raw --csv``): per timed kernel class found in the
@@ -175,26 +179,28 @@ def ingest_ncu(csv_path, precision, workload):
         if k == "stage":
             # the byte model is the average over the RKF45 stages: average the captured stage launches
             got = [r for r in data if (lambda mt: mt and mt.group(1).startswith(prefix))(
-                re.search(r"(k_\w+)<([^>]*)>", r[col["Kernel Name"]]))]
+                re.search(KNAME, r[col["Kernel Name"]]))]
             if got:
                 rd = sum(to_bytes(r, "dram__bytes_read.sum") for r in got) / len(got)
                 wr = sum(to_bytes(r, "dram__bytes_write.sum") for r in got) / len(got)
-                name = re.search(r"(k_\w+)<", got[0][col["Kernel Name"]]).group(1)
+                name = re.search(KNAME, got[0][col["Kernel Name"]]).group(1)
                 out[f"{k}/{precision}"] = {"kernel": f"{name} (average of {len(got)} stage launches)",
                                            "workload": workload, "bytes_per_launch": int(rd + wr), "read": int(rd),
                                            "write": int(wr), "source_sha": source_hash(k)}
             continue
         for r in data:
-            mt = re.search(r"(k_\w+)<([^>]*)>", r[col["Kernel Name"]])
+            mt = re.search(KNAME, r[col["Kernel Name"]])
             if not mt or not mt.group(1).startswith(prefix):
                 continue
+            targs = mt.group(2) or ""
             if k in ("yfwd", "yinv"):
                 # k_cols_reg / k_cols_tma<L1, L2, DIR, PIN, POUT>: DIR is the third argument
-                direction = int(mt.group(2).split(",")[2].replace("(int)", "").strip())
+                direction = int(targs.split(",")[2].replace("(int)", "").strip())
                 if (direction < 0) != (k == "yfwd"):
                     continue
             rd, wr = to_bytes(r, "dram__bytes_read.sum"), to_bytes(r, "dram__bytes_write.sum")
-            out[f"{k}/{precision}"] = {"kernel": f"{mt.group(1)}<{mt.group(2)}>", "workload": workload,
+            out[f"{k}/{precision}"] = {"kernel": mt.group(1) + (f"<{targs}>" if mt.group(2) is not None else ""),
+                                       "workload": workload,
                                        "bytes_per_launch": int(rd + wr), "read": int(rd), "write": int(wr),
                                        "source_sha": source_hash(k)}
             break

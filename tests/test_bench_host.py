@@ -46,7 +46,7 @@ ROWS = [
     ("void k_cols_reg<32, 32, (int)-1, 1, 0>(const float2 *)", 100.0, 150000.0),
     ("void k_zconv_reg<32>(float2 *)", 300.0, 150000.0),
     ("void k_cols_reg<32, 32, 1, 0, 1>(const float2 *)", 200.0, 70000.0),
-    ("void k_xinv_reg<32, 16>(const float2 *)", 100.0, 20000.0),
+    ("void unnamed>::k_xinv_tma(const float2 *, float *)", 100.0, 20000.0),   # no template arguments
     ("void k_cols_reg<32, 32, (int)-1, 1, 0>(const float2 *)", 999.0, 999.0),   # later launch: ignored
 ] + [(f"void k_stage4<1, {s}>(Params<float>)", 200.0 + 10.0 * s, 60000.0) for s in range(6)]
 
