@@ -60,7 +60,8 @@ template <typename T, typename S> __device__ __forceinline__ T ld_r(S v) {
 //   or nullptr (scalar ms).  Complex length L = 2^lgL = Px / 2.
 //   Shared memory: B lines of L (FftGeom layout); global accesses run with
 //   the row index b fastest across a warp (B row segments per instruction).
-template <typename T, typename S = T>
+// HIN: nin <= L, so the upper half of every packed line is zero padding.
+template <typename T, typename S = T, bool HIN = false>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_xfwd(const S* __restrict__ in, long in_ld, int nin, const S* __restrict__ Ms, T ms,
                        long ms_rows, C_t<T>* __restrict__ out, int Hs, int lgL, long rows, int lgB,
                        const C_t<T>* __restrict__ twL, const C_t<T>* __restrict__ twP) {
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_xfwd(const S* _
         }
     }
     __syncthreads();
-    fft_lines<-1>(s, g, twL);
+    fft_lines<-1, HIN>(s, g, twL);
     const T half = (T)0.5;
     // X_k = E_k - i w^k D_k, E, D the even/odd split of the packed spectrum Z
     for (int idx = threadIdx.x; idx < total + B; idx += blockDim.x) {
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_xinv(const C_t<
         }
     }
     __syncthreads();
-    fft_lines<+1>(s, g, twL);
+    fft_lines<+1, false, true>(s, g, twL);   // only z[j], j < nx / 2 = L / 2, is kept
     const int lgP = ilog2(nx >> 1);
     for (int idx = threadIdx.x; idx < (B << lgP); idx += blockDim.x) {
         int b = idx & (B - 1), j = idx >> lgB;
@@ -188,7 +189,8 @@ __global__ void k_x1inv(const C_t<T>* __restrict__ in, int Hs, S* __restrict__ o
 // adjacent columns (kx) of one plane, loads nin rows (rest zero), transforms
 // length L = 2^lgL, stores nout rows.  Plane p: inner index p % n_inner,
 // outer p / n_inner.
-template <typename T, int DIR>
+// HIN: nin <= L/2 (the zero padding is the upper half); HOUT: nout <= L/2.
+template <typename T, int DIR, bool HIN = false, bool HOUT = false>
 __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_cols(const C_t<T>* in, C_t<T>* out, int lgL, int nin, int nout, int Hx, int lgB, ColGeom cg,
                        const C_t<T>* __restrict__ tw) {
     using C = C_t<T>;
@@ -219,7 +221,7 @@ __global__ void __launch_bounds__(sizeof(T) == 4 ? 1024 : 512) k_cols(const C_t<
         }
     }
     __syncthreads();
-    fft_lines<DIR>(s, g, tw);
+    fft_lines<DIR, HIN, HOUT>(s, g, tw);
     for (int idx = threadIdx.x; idx < (nout << lgB); idx += blockDim.x) {
         int b = idx & (B - 1), r = idx >> lgB;
         if (col0 + b < Hx) ob[r * cg.rs_out + col0 + b] = s[sidx(g, 0, r, b)];
@@ -261,7 +263,7 @@ __device__ __forceinline__ void zconv_one(C_t<T>* s, const T* kn, const FftGeom&
         }
     }
     __syncthreads();
-    fft_lines<-1>(s, g, twz);
+    fft_lines<-1, true>(s, g, twz);          // z >= nz = Pz / 2 is the zero padding
     const int ks = Pz2 << lgB;
     for (int idx = threadIdx.x; idx < (Pz << lgB); idx += blockDim.x) {
         int b = idx & (B - 1), kz = idx >> lgB;
@@ -279,7 +281,7 @@ __device__ __forceinline__ void zconv_one(C_t<T>* s, const T* kn, const FftGeom&
         s[o2] = cmk<C>(-(nxz * mx.x + nyz * my.x + nzz * mz.x), -(nxz * mx.y + nyz * my.y + nzz * mz.y));
     }
     __syncthreads();
-    fft_lines<+1>(s, g, twz);
+    fft_lines<+1, false, true>(s, g, twz);   // only z < nz is kept
     const int lgnz = lgPz > 0 ? lgPz - 1 : 0;               // nz = Pz / 2, or 1 when Pz = 1
     for (int idx = threadIdx.x; idx < 3 * (nz << lgB); idx += blockDim.x) {
         int b = idx & (B - 1), rest = idx >> lgB;       // rest = c * nz + z
@@ -1407,9 +1409,10 @@ int run_xfwd(mm_ctx* ctx, const T* in, long in_ld, int nin, const T* Ms, T ms, l
     }
     const int B = x_rows_per_block(L);
     size_t smem = (size_t)L * B * sizeof(C_t<T>);
-    int rc = set_smem(ctx, (const void*)k_xfwd<T>, smem);
+    auto fn = nin <= L ? k_xfwd<T, T, true> : k_xfwd<T, T, false>;
+    int rc = set_smem(ctx, (const void*)fn, smem);
     if (rc) return rc;
-    k_xfwd<T><<<(unsigned)((rows + B - 1) / B), block_threads(B * L / 8), smem, ctx->stream>>>(
+    fn<<<(unsigned)((rows + B - 1) / B), block_threads(B * L / 8), smem, ctx->stream>>>(
         in, in_ld, nin, Ms, ms, ms_rows, out, ctx->Hs, ilog2(L), rows, ilog2(B), twL, twP);
     MM_LAUNCH_CHECK(ctx);
     return MM_OK;
@@ -1569,10 +1572,13 @@ int run_cols(mm_ctx* ctx, const C_t<T>* in, C_t<T>* out, int L, int nin, int nou
     }
     const int B = col_tile(L, sizeof(C_t<T>));
     size_t smem = (size_t)L * B * sizeof(C_t<T>);
-    int rc = set_smem(ctx, (const void*)k_cols<T, DIR>, smem);
+    const bool hin = 2 * nin <= L, hout = 2 * nout <= L;
+    auto fn = hin ? (hout ? k_cols<T, DIR, true, true> : k_cols<T, DIR, true, false>)
+                  : (hout ? k_cols<T, DIR, false, true> : k_cols<T, DIR, false, false>);
+    int rc = set_smem(ctx, (const void*)fn, smem);
     if (rc) return rc;
     dim3 grid((unsigned)((ctx->Hx + B - 1) / B), (unsigned)nplanes);
-    k_cols<T, DIR><<<grid, block_threads(B * L / 8), smem, ctx->stream>>>(in, out, ilog2(L), nin, nout, ctx->Hx,
+    fn<<<grid, block_threads(B * L / 8), smem, ctx->stream>>>(in, out, ilog2(L), nin, nout, ctx->Hx,
                                                                           ilog2(B), g, tw);
     MM_LAUNCH_CHECK(ctx);
     return MM_OK;
@@ -1818,8 +1824,9 @@ int apply_ff(mm_ctx* ctx, const double* m, double* H, bool unit) {
             const int L = ctx->Px / 2;
             const int B = x_rows_per_block(L);
             const size_t smem = (size_t)L * B * sizeof(C);
-            if ((rc = set_smem(ctx, (const void*)k_xfwd<ff, double>, smem))) return rc;
-            k_xfwd<ff, double><<<(unsigned)((rows + B - 1) / B), block_threads(B * L / 8), smem, ctx->stream>>>(
+            // nin = nx = L: the upper half of each packed line is zero padding
+            if ((rc = set_smem(ctx, (const void*)k_xfwd<ff, double, true>, smem))) return rc;
+            k_xfwd<ff, double, true><<<(unsigned)((rows + B - 1) / B), block_threads(B * L / 8), smem, ctx->stream>>>(
                 m, ctx->nx, ctx->nx, Ms, ms, ms_rows, xout, ctx->Hs, ilog2(L), rows, ilog2(B), tw + ctx->tw.off_lx,
                 tw + ctx->tw.off_px);
         }
