@@ -225,8 +225,17 @@ enum {
  * Turning it on clears the accumulated times. */
 int mm_enable_kernel_timing(mm_ctx* ctx, int enable);
 
-/* Waits for the stream, then reports the summed device time (ms) and the
- * launch count of kernel class `kernel` since timing was enabled. */
+/* The same for a subset of kernel classes (no paper counterpart):
+ * bit k of `classes` (k < MM_K_COUNT) brackets the launches of class k with
+ * events; launches of every class are counted while any bit is set; 0 turns
+ * timing off.  Each event pair costs device time, so timing one class keeps
+ * the measured stretch closer to an uninstrumented run.  Clears the
+ * accumulated times.  Errors: INVALID_ARG (bits above MM_K_COUNT). */
+int mm_enable_kernel_timing_mask(mm_ctx* ctx, unsigned classes);
+
+/* Waits for the stream, then reports the summed device time (ms, 0 for a
+ * class outside the timing mask) and the launch count of kernel class
+ * `kernel` since timing was enabled. */
 int mm_kernel_time(mm_ctx* ctx, int kernel, double* total_ms, long* launches);
 
 /* After any call that waited for the stream (llg_step, relax, energy,

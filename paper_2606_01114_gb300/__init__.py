@@ -77,6 +77,7 @@ def _load():
         "mm_last_error": (ctypes.c_char_p, [P]),
         "mm_kernel_launches": (L, [P]),
         "mm_enable_kernel_timing": (I, [P, I]),
+        "mm_enable_kernel_timing_mask": (I, [P, ctypes.c_uint]),
         "mm_kernel_time": (I, [P, I, DP, LP]),
         "mm_step_stats": (I, [P, LP, LP, DP, DP]),
         "mm_energy_noalloc": (I, [I, I, I, D, D, D, I, D, D, D, DP, DP, P, P, DP, P]),
@@ -317,6 +318,12 @@ def mm_kernel_launches(ctx):
 
 def mm_enable_kernel_timing(ctx, enable=True):
     _check(ctx, _load().mm_enable_kernel_timing(ctx.handle, 1 if enable else 0))
+
+
+def mm_enable_kernel_timing_mask(ctx, classes):
+    """Time only the kernel classes whose bits are set in `classes` (every
+    class's launches are still counted); 0 turns timing off."""
+    _check(ctx, _load().mm_enable_kernel_timing_mask(ctx.handle, int(classes)))
 
 
 def mm_kernel_time(ctx, kernel):

@@ -47,14 +47,16 @@ void harvest_timing(mm_ctx* ctx) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, ctx->ev_pool[2 * i], ctx->ev_pool[2 * i + 1]) == cudaSuccess) {
             ctx->kt_ms[ctx->ev_kind[i]] += ms;
-            ctx->kt_n[ctx->ev_kind[i]] += 1;
         }
     }
     cudaGetLastError();
     ctx->ev_used = 0;
 }
 
-KernelTimer::KernelTimer(mm_ctx* c, int kind) : ctx(c), slot(0), on(c->timing) {
+// Every launch of a class is counted while timing is on; the classes in the
+// mask are also bracketed by events (their device time is summed).
+KernelTimer::KernelTimer(mm_ctx* c, int kind) : ctx(c), slot(0), on(((c->timing >> kind) & 1u) != 0) {
+    if (c->timing) c->kt_n[kind] += 1;
     if (!on) return;
     if (ctx->ev_used >= 16384) harvest_timing(ctx);
     if (2 * (ctx->ev_used + 1) > ctx->ev_pool.size()) {
@@ -724,15 +726,20 @@ const char* mm_last_error(const mm_ctx* ctx) {
 
 long mm_kernel_launches(const mm_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
-int mm_enable_kernel_timing(mm_ctx* ctx, int enable) {
+int mm_enable_kernel_timing_mask(mm_ctx* ctx, unsigned classes) {
     if (!ctx) return fail(nullptr, MM_ERR_INVALID_ARG, "ctx is NULL");
+    if (classes >> MM_K_COUNT) return fail(ctx, MM_ERR_INVALID_ARG, "timing mask 0x%x names no kernel class", classes);
     harvest_timing(ctx);
     for (int k = 0; k < MM_K_COUNT; ++k) {
         ctx->kt_ms[k] = 0.0;
         ctx->kt_n[k] = 0;
     }
-    ctx->timing = enable != 0;
+    ctx->timing = classes;
     return MM_OK;
+}
+
+int mm_enable_kernel_timing(mm_ctx* ctx, int enable) {
+    return mm_enable_kernel_timing_mask(ctx, enable ? (1u << MM_K_COUNT) - 1u : 0u);
 }
 
 int mm_kernel_time(mm_ctx* ctx, int kernel, double* total_ms, long* launches) {

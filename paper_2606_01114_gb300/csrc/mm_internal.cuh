@@ -145,7 +145,7 @@ struct mm_ctx {
     std::string err;
 
     // per-kernel timing (mm_enable_kernel_timing)
-    bool timing;
+    unsigned timing;                    // bit k: bracket launches of kernel class k with events
     std::vector<cudaEvent_t> ev_pool;   // pairs (start, stop)
     std::vector<int> ev_kind;           // kernel class of each pair
     size_t ev_used;                     // pairs recorded since the last harvest

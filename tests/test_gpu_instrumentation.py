@@ -7,7 +7,10 @@
 * mm_llg_step_host, one step with the state in host memory (the end-to-end
   path the bench times): bit-identical to mm_llg_step on a device copy;
 * mm_alu_peak, the measured FMA roofs: positive, ordered as GB300's pipes
-  are (FP32 above FP64), and repeatable."""
+  are (FP32 above FP64), and repeatable;
+* mm_enable_kernel_timing_mask: only the masked classes carry device time,
+  every class's launches are still counted, and a bit above the classes is
+  rejected."""
 
 import numpy as np
 import pytest
@@ -108,3 +111,29 @@ def test_alu_peaks_are_measured():
     assert abs(again - f64) < 0.2 * f64
     with pytest.raises(mm.MMError):
         mm.mm_alu_peak(7)
+
+
+def test_kernel_timing_mask_times_only_the_masked_class():
+    n, d = (64, 32, 4), (2e-9, 2e-9, 2e-9)
+    ctx = mm.mm_init_mesh(*n, *d, precision=mm.MM_F32)
+    mm.mm_set_material(ctx, 8e5, 1.3e-11, 0.5, 0.0)
+    m = torch.tensor(wl.random_unit(n, seed=3), dtype=torch.float32, device="cuda")
+    zc, st = mm.KERNEL_NAMES.index("zconv"), mm.KERNEL_NAMES.index("stage")
+    mm.mm_enable_kernel_timing_mask(ctx, 1 << zc)
+    t, dt, _ = mm.mm_llg_step(ctx, m, 0.0, 1e-14, mm.MM_RKF45, 1e-5)
+    z_ms, z_n = mm.mm_kernel_time(ctx, zc)
+    s_ms, s_n = mm.mm_kernel_time(ctx, st)
+    assert z_n >= 6 and z_ms > 0.0
+    assert s_n == z_n and s_ms == 0.0
+    # all classes: the stage now carries device time too
+    mm.mm_enable_kernel_timing(ctx, True)
+    mm.mm_llg_step(ctx, m, t, dt, mm.MM_RKF45, 1e-5)
+    assert mm.mm_kernel_time(ctx, st)[0] > 0.0
+    # off: nothing counted
+    mm.mm_enable_kernel_timing_mask(ctx, 0)
+    mm.mm_llg_step(ctx, m, t, dt, mm.MM_RKF45, 1e-5)
+    assert mm.mm_kernel_time(ctx, zc) == (0.0, 0)
+    with pytest.raises(mm.MMError) as e:
+        mm.mm_enable_kernel_timing_mask(ctx, 1 << mm.MM_K_COUNT)
+    assert e.value.code == mm.MM_ERR_INVALID_ARG
+    mm.mm_destroy(ctx)
