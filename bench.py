@@ -665,33 +665,19 @@ def cufft_compare(mm, ctx, m, Ms, n, reps):
 def windows(run, steps, count, stream, kernel_timing=True, classes=("zconv",)):
     """Field evals/s of `count` further relax() windows of `steps` steps:
     median and 10th / 90th percentiles, timed like the headline (events
-    around the launches of `classes` only).  Without kernel timing (no event
-    at all) the evaluations are counted from the step statistics: six per
-    RKF45 trial plus relax()'s torque check before every ten trials and at
-    the end."""
+    around the launches of `classes` only).  Without kernel timing the only
+    events are those around the step controller's two launches per trial
+    (the evaluations are counted from the z-pass launches either way)."""
     import numpy as np
-    import torch
-    mm = run.mm
     vals = []
     for _ in range(count):
-        if kernel_timing:
-            r = run.timed(steps, stream, classes=classes)
-            vals.append(r["evals"] / (r["ms"] / 1e3))
-            continue
-        torch.cuda.synchronize()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        run.advance(steps)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        acc, rej, _, _ = mm.mm_step_stats(run.ctx)
-        trials = acc + rej
-        evals = 6 * trials + (trials + 9) // 10 + 1
-        vals.append(evals / (ev0.elapsed_time(ev1) / 1e3))
+        r = run.timed(steps, stream, classes=classes if kernel_timing else ("control",))
+        vals.append(r["evals"] / (r["ms"] / 1e3))
     return {"windows": count, "steps_each": steps, "median": float(np.median(vals)),
             "p10": float(np.percentile(vals, 10)), "p90": float(np.percentile(vals, 90)),
             "values": [round(v, 1) for v in vals],
-            "kernel_timing": ("events around " + ", ".join(classes) + " launches") if kernel_timing else False}
+            "kernel_timing": ("events around " + ", ".join(classes) + " launches") if kernel_timing
+            else "events around the step controller's launches only"}
 
 
 def measure_alu():

@@ -156,8 +156,9 @@ int mm_llg_step_host(mm_ctx* ctx, void* m_host, double* t, double* dt, int metho
                      double* err_out);
 
 /* RKF45 relaxation (tol 1e-5, first dt 1e-14 s) until
- * max_cells |m x H_eff| / Ms <= torque_tol (checked every 10 steps) or the
- * time reaches t_max.  *t_out, *steps_out (nullable) receive the simulated
+ * max_cells |m x H_eff| / Ms <= torque_tol (checked every 10 trial steps,
+ * sooner when fewer than 10 of the max_steps accepted steps remain) or the
+ * time reaches t_max.  At most max_steps steps are accepted.  *t_out, *steps_out (nullable) receive the simulated
  * time and accepted step count.  Step-size control stays on the device.
  * Errors: NOT_CONVERGED when max_steps is reached first, NONFINITE,
  * DT_UNDERFLOW, TIMEOUT (a bounded device wait gave up), CUDA. */

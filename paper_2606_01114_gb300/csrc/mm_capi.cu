@@ -470,7 +470,11 @@ int mm_relax(mm_ctx* ctx, void* m, double t_max, double torque_tol, long max_ste
         if (tq <= torque_tol || c->done) return MM_OK;
         if (c->steps >= max_steps || attempts >= max_attempts)
             return fail(ctx, MM_ERR_NOT_CONVERGED, "relax stopped after %lld steps, torque %.3e", (long long)c->steps, tq);
-        for (int k = 0; k < kCheck; ++k, ++attempts)
+        // each trial accepts at most one step: a batch no longer than the
+        // steps still allowed stops relax at exactly max_steps
+        const long room = max_steps - (long)c->steps;
+        const int batch = room < kCheck ? (int)room : kCheck;
+        for (int k = 0; k < batch; ++k, ++attempts)
             if ((rc = trial(ctx, m, MM_RKF45))) return rc;
     }
 }

@@ -392,6 +392,8 @@ def test_error_paths_underflow_and_step_cap():
     with pytest.raises(mm.MMError) as e:
         mm.mm_relax(ctx, md, t_max=1e-6, torque_tol=1e-12, max_steps=20)
     assert e.value.code == mm.MM_ERR_NOT_CONVERGED
+    # the step cap is exact, rejected trials or not
+    assert mm.mm_step_stats(ctx)[0] == 20
     t, dt, err = mm.mm_llg_step(ctx, md, 0.0, 1e-14, mm.MM_RKF45, tol=1e-5)   # still usable
     assert t > 0 and err <= 1e-5
     mm.mm_destroy(ctx)
