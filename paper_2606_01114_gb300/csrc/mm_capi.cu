@@ -11,6 +11,12 @@
 #include "mm_internal.cuh"
 
 namespace mm {
+// mm_exchange.cu: four-cell FP32 field kernels for uniform material (*done
+// false when the context does not qualify)
+int field4(mm_ctx* ctx, const void* m, const void* Hd, void* H, bool effective, bool* done);
+}  // namespace mm
+
+namespace mm {
 
 static thread_local std::string g_init_error;
 
@@ -380,6 +386,9 @@ int mm_exchange_field(mm_ctx* ctx, const void* m, void* H) {
     if (!ctx) return fail(nullptr, MM_ERR_INVALID_ARG, "ctx is NULL");
     MM_BIND(ctx);
     if (!m || !H) return fail(ctx, MM_ERR_INVALID_ARG, "m and H must be device pointers");
+    bool done = false;
+    int rc = field4(ctx, m, nullptr, H, false, &done);
+    if (rc || done) return rc;
     return field_exchange(ctx, m, H);
 }
 
@@ -389,6 +398,9 @@ int mm_effective_field(mm_ctx* ctx, const void* m, void* H) {
     if (!m || !H) return fail(ctx, MM_ERR_INVALID_ARG, "m and H must be device pointers");
     int rc = demag_apply(ctx, m, ctx->Hd);
     if (rc) return rc;
+    bool done = false;
+    rc = field4(ctx, m, ctx->Hd, H, true, &done);
+    if (rc || done) return rc;
     return field_effective(ctx, m, ctx->Hd, H);
 }
 

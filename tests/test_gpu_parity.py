@@ -167,6 +167,29 @@ def test_exchange_and_effective_field(prec):
     mm.mm_destroy(ctx)
 
 
+# uniform material, nx a multiple of 4: the four-cell FP32 field kernels
+# (x edges inside and across the quads, one-cell-thick axes); FP64 takes the
+# generic kernel on the same inputs
+@pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
+@pytest.mark.parametrize("n,d", [((16, 8, 4), (2e-9, 2.5e-9, 3e-9)), ((4, 6, 1), (2e-9, 2e-9, 2e-9)),
+                                 ((64, 32, 2), (3e-9, 2e-9, 4e-9))])
+def test_exchange_and_effective_field_uniform_material(n, d, prec):
+    p = micromag.Problem(n, d, Ku=3e5, u=(0.3, -0.2, 0.9), h_ext=(1e4, -2e4, 3e4))
+    m = wl.random_unit(n, seed=9)
+    ctx = mm.mm_init_mesh(*n, *d, precision=prec)
+    mm.mm_set_material(ctx, 8e5, 1.3e-11, 0.02, 3e5, (0.3, -0.2, 0.9))
+    mm.mm_set_external_field(ctx, 1e4, -2e4, 3e4)
+    H = torch.empty(ctx.shape3, dtype=torch.float64 if prec == mm.MM_F64 else torch.float32, device="cuda")
+    md = dev(m, prec)
+    mm.mm_exchange_field(ctx, md, H)
+    got, ref = host(H), p.exchange(m)
+    assert rel_l2(got, ref) < TOL[prec]
+    assert np.max(np.abs(got - ref)) < 10 * TOL[prec] * np.max(np.abs(ref))
+    mm.mm_effective_field(ctx, md, H)
+    assert rel_l2(host(H), p.h_eff(m)) < TOL[prec]
+    mm.mm_destroy(ctx)
+
+
 def test_rk4_film64_200_steps_fp64():
     """64 x 64 x 4 permalloy film, random m, 200 RK4 steps at dt = 1e-13 s.
 
