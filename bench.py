@@ -909,7 +909,7 @@ def run_ours(args):
     if extras:
         line["windows"] = windows(run, 20, 5, stream, classes=(dom,))
         if args.solver == "relax":
-            line["windows_without_kernel_events"] = windows(run, 20, 5, stream, kernel_timing=False)
+            line["windows_controller_events_only"] = windows(run, 20, 5, stream, kernel_timing=False)
         if args.solver == "relax" and prec == mm.MM_F32 and args.fft_mode == "fp32" and not (args.dmi or args.stt):
             line["cufft"] = {"f32": cufft_compare(mm, ctx, m, w["Ms"], n, 20)}
             line["cufft"]["f32"]["ours_demag_ms_per_eval"] = line["demag_ms_per_eval"]
